@@ -1,0 +1,707 @@
+/*
+ * escape_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU restatement of what the ESCAPE census
+ * computes (Pinar, Seshadhri, Vishal, "ESCAPE: Efficiently Counting All
+ * 5-Vertex Subgraphs", arXiv 1610.09411).  It exists to check the CUDA path
+ * and is used only by the tests, the entry point's smoke check and the
+ * benchmark's CPU-baseline leg.  It shares no code, table or header with the
+ * CUDA library.
+ *
+ * Two tiers:
+ *   O1  oracle_brute_census: the definition itself -- every k-subset
+ *       (k = 3, 4, 5) is classified by canonical form (Sec. 3.1); only for
+ *       small n.
+ *   O2  oracle_census_sums: per-vertex / per-edge quantities computed from
+ *       their plain definitions (common-neighbour lists by sorted merge,
+ *       per-vertex two-hop pair counts), then the sums that the paper's
+ *       closed forms (Thms 4, 8-11, 13, 14; App. A) are built from.  The
+ *       closed forms themselves are assembled in exact Python integers in
+ *       oracle/__init__.py.
+ *
+ * Input: simple undirected graph as CSR (row_ptr int64[n+1], col int32[nnz]),
+ * neighbour lists sorted ascending, symmetric, no loops or duplicates.
+ * Degree order (Sec. 3.2): i < j iff d(i) < d(j), or d(i) = d(j) and i < j.
+ * All sums are unsigned 128-bit with overflow detection; any overflow makes
+ * the call return ORACLE_EOVERFLOW.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2, ORACLE_EOVERFLOW = 4 };
+
+/* ------------------------------------------------------------------ */
+/* Pattern catalogue.  5-vertex connected patterns 1..21 follow the    */
+/* paper's figure of all connected 5-vertex patterns (tikz macros       */
+/* \pone..\ptwentyone); 22..32 follow its figure of disconnected         */
+/* 5-vertex patterns; 33 (P3 + K2) and 34 (K3 + K2) complete the 34     */
+/* isomorphism classes (the paper's disconnected figure omits these two). */
+/* Vertices are the paper's labels 1..5; edges written as two digits.    */
+/* ------------------------------------------------------------------ */
+static const char* const CAT5[34] = {
+  "12 13 14 15",                     /* 1  4-star                       */
+  "12 13 14 25",                     /* 2                               */
+  "12 13 24 35",                     /* 3  path P5                      */
+  "12 13 23 34 35",                  /* 4                               */
+  "12 13 23 24 45",                  /* 5                               */
+  "12 13 23 24 35",                  /* 6                               */
+  "12 13 24 34 35",                  /* 7                               */
+  "12 13 24 35 45",                  /* 8  5-cycle                      */
+  "12 13 23 34 35 45",               /* 9  bowtie                       */
+  "12 13 14 24 34 35",               /* 10                              */
+  "12 13 23 24 34 35",               /* 11                              */
+  "12 13 24 34 35 45",               /* 12 house                        */
+  "12 13 14 25 35 45",               /* 13 K2,3                         */
+  "12 13 14 15 25 35 45",            /* 14                              */
+  "12 13 14 23 24 34 35",            /* 15 K4 + pendant                 */
+  "12 13 23 24 34 35 45",            /* 16                              */
+  "12 13 14 23 24 35 45",            /* 17                              */
+  "12 13 14 15 23 24 35 45",         /* 18 wheel                        */
+  "12 13 14 23 24 34 35 45",         /* 19                              */
+  "13 14 15 23 24 25 34 35 45",      /* 20 K5 minus an edge             */
+  "12 13 14 15 23 24 25 34 35 45",   /* 21 K5                           */
+  "",                                /* 22 5K1                          */
+  "12",                              /* 23 K2 + 3K1                     */
+  "12 34",                           /* 24 2K2 + K1                     */
+  "12 23",                           /* 25 P3 + 2K1                     */
+  "12 13 23",                        /* 26 K3 + 2K1                     */
+  "12 13 14",                        /* 27 3-star + K1                  */
+  "12 13 24",                        /* 28 P4 + K1                      */
+  "12 13 14 23",                     /* 29 tailed triangle + K1         */
+  "12 13 24 34",                     /* 30 C4 + K1                      */
+  "12 13 14 23 24",                  /* 31 diamond + K1                 */
+  "12 13 14 23 24 34",               /* 32 K4 + K1                      */
+  "12 23 45",                        /* 33 P3 + K2                      */
+  "12 13 23 45",                     /* 34 K3 + K2                      */
+};
+/* 4-vertex: connected patterns of the paper's 4-vertex figure (3-star,
+ * 3-path, tailed triangle, 4-cycle, diamond, 4-clique), then its
+ * disconnected 4-vertex figure (independent set, edge, matching, wedge,
+ * triangle). */
+static const char* const CAT4[11] = {
+  "12 13 14", "12 13 24", "12 13 14 23", "12 13 24 34", "12 13 14 23 24",
+  "12 13 14 23 24 34", "", "12", "12 34", "12 23", "12 13 23",
+};
+/* 3-vertex: empty, edge, wedge, triangle. */
+static const char* const CAT3[4] = { "", "12", "12 13", "12 13 23" };
+
+static int pair_index(int k, int a, int b) { /* a < b, 0-based, bit of pair */
+  int idx = 0;
+  for (int x = 0; x < k; ++x)
+    for (int y = x + 1; y < k; ++y, ++idx)
+      if (x == a && y == b) return idx;
+  return -1;
+}
+
+static int parse_mask(int k, const char* s) {
+  int mask = 0;
+  for (const char* p = s; *p; ++p) {
+    if (*p >= '1' && *p <= '9' && p[1] >= '1' && p[1] <= '9') {
+      int a = p[0] - '1', b = p[1] - '1';
+      if (a > b) { int t = a; a = b; b = t; }
+      mask |= 1 << pair_index(k, a, b);
+      ++p;
+    }
+  }
+  return mask;
+}
+
+static int permute_mask(int k, int mask, const int* perm) {
+  int out = 0, idx = 0;
+  for (int x = 0; x < k; ++x)
+    for (int y = x + 1; y < k; ++y, ++idx)
+      if (mask >> idx & 1) {
+        int a = perm[x], b = perm[y];
+        if (a > b) { int t = a; a = b; b = t; }
+        out |= 1 << pair_index(k, a, b);
+      }
+  return out;
+}
+
+/* canonical form = smallest mask over all k! relabellings */
+static int canon(int k, int mask) {
+  int perm[5] = {0, 1, 2, 3, 4}, best = 1 << 30;
+  /* iterate permutations (Heap's algorithm, iterative) */
+  int c[5] = {0}, i = 0;
+  int v = permute_mask(k, mask, perm);
+  if (v < best) best = v;
+  while (i < k) {
+    if (c[i] < i) {
+      int a = (i % 2 == 0) ? 0 : c[i];
+      int t = perm[a]; perm[a] = perm[i]; perm[i] = t;
+      v = permute_mask(k, mask, perm);
+      if (v < best) best = v;
+      ++c[i]; i = 0;
+    } else { c[i] = 0; ++i; }
+  }
+  return best;
+}
+
+static int g_tables_ready = 0;
+static signed char g_cls3[8], g_cls4[64], g_cls5[1024];
+static int g_rep3[4], g_rep4[11], g_rep5[34];
+
+static int build_tables(void) {
+  if (g_tables_ready) return 0;
+  const char* const* cats[3] = {CAT3, CAT4, CAT5};
+  int ks[3] = {3, 4, 5}, ncls[3] = {4, 11, 34};
+  signed char* tabs[3] = {g_cls3, g_cls4, g_cls5};
+  int* reps[3] = {g_rep3, g_rep4, g_rep5};
+  for (int t = 0; t < 3; ++t) {
+    int k = ks[t], npairs = k * (k - 1) / 2;
+    int cf[34];
+    for (int c = 0; c < ncls[t]; ++c) {
+      reps[t][c] = parse_mask(k, cats[t][c]);
+      cf[c] = canon(k, reps[t][c]);
+      for (int d = 0; d < c; ++d) if (cf[d] == cf[c]) return ORACLE_EINVAL; /* duplicate class */
+    }
+    for (int mask = 0; mask < (1 << npairs); ++mask) {
+      int f = canon(k, mask), cls = -1;
+      for (int c = 0; c < ncls[t]; ++c) if (cf[c] == f) cls = c;
+      if (cls < 0) return ORACLE_EINVAL;                               /* catalogue incomplete */
+      tabs[t][mask] = (signed char)cls;
+    }
+  }
+  g_tables_ready = 1;
+  return 0;
+}
+
+/* Class id (0-based) of a k-vertex graph given by its pair mask. */
+int oracle_classify(int k, int mask) {
+  if (build_tables()) return -1;
+  if (k == 3) return g_cls3[mask & 7];
+  if (k == 4) return g_cls4[mask & 63];
+  if (k == 5) return g_cls5[mask & 1023];
+  return -1;
+}
+
+/* A[i][j] = number of spanning subgraphs (all k vertices, a subset of the
+ * edges) of class j's graph that are isomorphic to class i (App. B: N = A C).
+ * Written row-major into A (ncls x ncls). */
+int oracle_matrix(int k, int64_t* A) {
+  if (build_tables()) return ORACLE_EINVAL;
+  int ncls = k == 3 ? 4 : (k == 4 ? 11 : (k == 5 ? 34 : 0));
+  if (!ncls) return ORACLE_EINVAL;
+  const int* reps = k == 3 ? g_rep3 : (k == 4 ? g_rep4 : g_rep5);
+  memset(A, 0, sizeof(int64_t) * ncls * ncls);
+  for (int j = 0; j < ncls; ++j) {
+    int e = reps[j];
+    /* every subset of the edge set of class j */
+    for (int sub = e;; sub = (sub - 1) & e) {
+      A[oracle_classify(k, sub) * ncls + j] += 1;
+      if (sub == 0) break;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* O1: brute force over every k-subset (the definition, Sec. 3.1).      */
+/* ------------------------------------------------------------------ */
+static int has_edge(const int64_t* rp, const int32_t* col, int64_t u, int64_t v) {
+  int64_t lo = rp[u], hi = rp[u + 1];
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (col[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo < rp[u + 1] && col[lo] == v;
+}
+
+int oracle_brute_census(int64_t n, const int64_t* rp, const int32_t* col,
+                        uint64_t* c3, uint64_t* c4, uint64_t* c5) {
+  if (build_tables()) return ORACLE_EINVAL;
+  if (n > 200) return ORACLE_EINVAL;
+  memset(c3, 0, 4 * sizeof(uint64_t));
+  memset(c4, 0, 11 * sizeof(uint64_t));
+  memset(c5, 0, 34 * sizeof(uint64_t));
+  unsigned char* adj = (unsigned char*)calloc((size_t)(n > 0 ? n * n : 1), 1);
+  if (!adj) return ORACLE_ENOMEM;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) adj[u * n + col[p]] = 1;
+  int64_t v[5];
+  for (v[0] = 0; v[0] < n; ++v[0])
+    for (v[1] = v[0] + 1; v[1] < n; ++v[1])
+      for (v[2] = v[1] + 1; v[2] < n; ++v[2]) {
+        int m3 = (adj[v[0] * n + v[1]]) | (adj[v[0] * n + v[2]] << 1) | (adj[v[1] * n + v[2]] << 2);
+        c3[g_cls3[m3]]++;
+        for (v[3] = v[2] + 1; v[3] < n; ++v[3]) {
+          int m4 = 0, idx = 0;
+          for (int x = 0; x < 4; ++x)
+            for (int y = x + 1; y < 4; ++y, ++idx) m4 |= adj[v[x] * n + v[y]] << idx;
+          c4[g_cls4[m4]]++;
+          for (v[4] = v[3] + 1; v[4] < n; ++v[4]) {
+            int m5 = 0; idx = 0;
+            for (int x = 0; x < 5; ++x)
+              for (int y = x + 1; y < 5; ++y, ++idx) m5 |= adj[v[x] * n + v[y]] << idx;
+            c5[g_cls5[m5]]++;
+          }
+        }
+      }
+  free(adj);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* O2: the paper's method, written plainly.                            */
+/* ------------------------------------------------------------------ */
+static int g_ovf;
+static u128 add(u128 a, u128 b) { u128 s = a + b; if (s < a) g_ovf = 1; return s; }
+static u128 mul(u128 a, u128 b) {
+  if (a != 0 && b > ((u128)0 - 1) / a) g_ovf = 1;
+  return a * b;
+}
+static u128 ch2(uint64_t x) { return x < 2 ? 0 : (u128)x * (x - 1) / 2; }
+static u128 ch3(uint64_t x) { return x < 3 ? 0 : ch2(x) * (x - 2) / 3; }
+static u128 ch4(uint64_t x) { return x < 4 ? 0 : ch3(x) * (x - 3) / 4; }
+
+/* Indices of the sums returned by oracle_census_sums (each 2 x u64, lo/hi). */
+enum {
+  S_N, S_M, S_W, S_S3, S_S4, S_T, S_EDGE_DD /* sum_e (d_i-1)(d_j-1) */, S_TT,
+  S_C4, S_D, S_K4, S_N2A, S_N3A, S_N4, S_N5A, S_N6A, S_N7A, S_N8M, S_N8Z, S_N9A,
+  S_N10A, S_N11, S_N12A, S_N13, S_N14, S_N15, S_N16A, S_N17, S_N18X4, S_N19,
+  S_N20, S_N21, S_WM /* W*m */, S_D2D /* sum_c C(d_c,2) d_c */,
+  S_DNBR /* sum_c (d_c-1) sum_{a in N(c)} d_a */, S_TM /* T*m */, S_TD /* sum_i t_i d_i */,
+  S_COUNT
+};
+
+int oracle_num_sums(void) { return S_COUNT; }
+
+typedef struct {
+  int64_t n;
+  const int64_t* rp;
+  const int32_t* col;
+  int64_t* deg;
+  /* full common-neighbour list of every CSR slot p = (u -> v):
+   * U[uoff[p] .. uoff[p+1]) = N(u) cap N(v), sorted */
+  int64_t* uoff;
+  int32_t* U;
+  int64_t* rev;   /* rev[p] = slot of (v -> u) */
+} G;
+
+static int prec(const G* g, int64_t a, int64_t b) {  /* a precedes b in the degree order */
+  return g->deg[a] < g->deg[b] || (g->deg[a] == g->deg[b] && a < b);
+}
+
+static int64_t slot_of(const G* g, int64_t u, int64_t v) {
+  int64_t lo = g->rp[u], hi = g->rp[u + 1];
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (g->col[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return (lo < g->rp[u + 1] && g->col[lo] == v) ? lo : -1;
+}
+
+static int64_t merge_count(const int32_t* a, int64_t na, const int32_t* b, int64_t nb) {
+  int64_t i = 0, j = 0, c = 0;
+  while (i < na && j < nb) {
+    if (a[i] < b[j]) ++i; else if (a[i] > b[j]) ++j; else { ++c; ++i; ++j; }
+  }
+  return c;
+}
+
+static int validate(int64_t n, const int64_t* rp, const int32_t* col) {
+  if (n < 0 || rp[0] != 0) return ORACLE_EINVAL;
+  for (int64_t u = 0; u < n; ++u) {
+    if (rp[u + 1] < rp[u]) return ORACLE_EINVAL;
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+      if (col[p] < 0 || col[p] >= n || col[p] == u) return ORACLE_EINVAL;
+      if (p > rp[u] && col[p] <= col[p - 1]) return ORACLE_EINVAL;
+    }
+  }
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p)
+      if (!has_edge(rp, col, col[p], u)) return ORACLE_EINVAL;
+  return ORACLE_OK;
+}
+
+static void free_g(G* g) { free(g->deg); free(g->uoff); free(g->U); free(g->rev); }
+
+static int setup(G* g, int64_t n, const int64_t* rp, const int32_t* col) {
+  memset(g, 0, sizeof(*g));
+  g->n = n; g->rp = rp; g->col = col;
+  int64_t nnz = n > 0 ? rp[n] : 0;
+  g->deg = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  g->uoff = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
+  g->rev = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
+  if (!g->deg || !g->uoff || !g->rev) return ORACLE_ENOMEM;
+  for (int64_t u = 0; u < n; ++u) g->deg[u] = rp[u + 1] - rp[u];
+  /* T(e) = |N(u) cap N(v)| for every slot, then the lists themselves */
+  g->uoff[0] = 0;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+      int64_t v = col[p];
+      g->uoff[p + 1] = g->uoff[p] + merge_count(col + rp[u], g->deg[u], col + rp[v], g->deg[v]);
+      g->rev[p] = slot_of(g, v, u);
+    }
+  g->U = (int32_t*)malloc(sizeof(int32_t) * (g->uoff[nnz] + 1));
+  if (!g->U) return ORACLE_ENOMEM;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+      int64_t v = col[p], i = rp[u], j = rp[v], w = g->uoff[p];
+      while (i < rp[u + 1] && j < rp[v + 1]) {
+        if (col[i] < col[j]) ++i; else if (col[i] > col[j]) ++j;
+        else { g->U[w++] = col[i]; ++i; ++j; }
+      }
+    }
+  return ORACLE_OK;
+}
+
+#define TE(p) ((uint64_t)(g.uoff[(p) + 1] - g.uoff[(p)]))
+
+/*
+ * Per-element outputs (any may be NULL), indexed like the input:
+ *   Te[p], C4e[p], K4e[p] per CSR slot p (both slots of an edge agree);
+ *   ti[v], C4i[v], K4i[v] per vertex.
+ * sums: S_COUNT entries of two u64 words (lo, hi) each.
+ */
+int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_t* sums,
+                       uint64_t* Te_out, uint64_t* ti_out, uint64_t* C4e_out, uint64_t* C4i_out,
+                       uint64_t* K4e_out, uint64_t* K4i_out) {
+  int rc = validate(n, rp, col);
+  if (rc) return rc;
+  G g;
+  rc = setup(&g, n, rp, col);
+  if (rc) { free_g(&g); return rc; }
+  g_ovf = 0;
+  int64_t nnz = n > 0 ? rp[n] : 0;
+  u128 S[S_COUNT];
+  memset(S, 0, sizeof(S));
+
+  uint64_t* t = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+  uint64_t* C4e = (uint64_t*)calloc((size_t)nnz + 1, sizeof(uint64_t));
+  uint64_t* C4i = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+  uint64_t* K4e = (uint64_t*)calloc((size_t)nnz + 1, sizeof(uint64_t));
+  uint64_t* K4i = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));   /* W(i, .) */
+  int64_t* cc = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));    /* cc(i, .) */
+  int64_t* wp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));    /* w'(i, .) */
+  int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  int64_t* stamp2 = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  int64_t* touched = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  int64_t *outp = NULL, *stamp3 = NULL;
+  int32_t* outc = NULL;
+  if (!t || !C4e || !C4i || !K4e || !K4i || !cnt || !cc || !wp || !stamp || !stamp2 || !touched || !pos) {
+    rc = ORACLE_ENOMEM; goto done;
+  }
+  for (int64_t v = 0; v <= n; ++v) { stamp[v] = -1; stamp2[v] = -1; }
+
+  /* ---- degrees, wedges, stars (Thm 4) ---- */
+  S[S_N] = (u128)n;
+  S[S_M] = (u128)(nnz / 2);
+  for (int64_t i = 0; i < n; ++i) {
+    S[S_W] = add(S[S_W], ch2(g.deg[i]));
+    S[S_S3] = add(S[S_S3], ch3(g.deg[i]));
+    S[S_S4] = add(S[S_S4], ch4(g.deg[i]));            /* N1 (Thm 8) */
+  }
+
+  /* ---- triangles per vertex: t(i) = (1/2) sum_{j in N(i)} T(i,j) ---- */
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t s = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += TE(p);
+    t[i] = s / 2;
+  }
+  for (int64_t i = 0; i < n; ++i) S[S_T] = add(S[S_T], t[i]);
+  S[S_T] /= 3;
+  for (int64_t i = 0; i < n; ++i)
+    if (g.deg[i] >= 2) S[S_TT] = add(S[S_TT], mul(t[i], (uint64_t)(g.deg[i] - 2)));   /* tailed triangles */
+
+  /* ---- per-edge sums over unordered edges e = {i, j} (Thms 4, 9) ---- */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = col[p];
+      uint64_t te = TE(p), di = (uint64_t)g.deg[i], dj = (uint64_t)g.deg[j];
+      /* ordered sums: every slot (i -> j) */
+      S[S_N2A] = add(S[S_N2A], mul(ch2(di - 1), dj - 1));                 /* N2 first term */
+      S[S_N5A] = add(S[S_N5A], mul(t[i] - te, dj - 1));                   /* N5 first term */
+      if (te >= 2) S[S_N11] = add(S[S_N11], mul(ch2(te), di - 3));         /* N11 */
+      if (i < j) {   /* unordered */
+        S[S_EDGE_DD] = add(S[S_EDGE_DD], mul(di - 1, dj - 1));
+        S[S_D] = add(S[S_D], ch2(te));                                     /* diamonds */
+        if (te) S[S_N6A] = add(S[S_N6A], mul(mul(te, di - 2), dj - 2));    /* N6 first term */
+        S[S_N14] = add(S[S_N14], ch3(te));                                 /* N14 */
+      }
+    }
+
+  /* ---- N3 first term: sum_i sum_{j<k in N(i)} (d_j-1)(d_k-1) (Thm 8) ---- */
+  for (int64_t i = 0; i < n; ++i) {
+    u128 s1 = 0, s2 = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      uint64_t x = (uint64_t)g.deg[col[p]] - 1;
+      s1 = add(s1, x);
+      s2 = add(s2, mul(x, x));
+    }
+    S[S_N3A] = add(S[S_N3A], (mul(s1, s1) - s2) / 2);
+  }
+  /* N4 = sum_i t(i) C(d(i)-2, 2); N9 first term = sum_i C(t(i), 2) (Thm 8) */
+  for (int64_t i = 0; i < n; ++i) {
+    if (g.deg[i] >= 2) S[S_N4] = add(S[S_N4], mul(t[i], ch2((uint64_t)g.deg[i] - 2)));
+    S[S_N9A] = add(S[S_N9A], ch2(t[i]));
+  }
+
+  /* ---- per-edge and per-triangle 4-clique counts.  For an edge u < v (by
+   * id) and x in U(u,v), the triangle {u, v, x} lies in |U(u,v) cap U(u,x)|
+   * 4-cliques (its common neighbours); K4(e) is half the sum over x (Thm 7).
+   * U(u,v) is marked in `stamp` so each intersection is one scan of U(u,x). */
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+      int64_t v = col[p];
+      if (v < u) continue;
+      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) stamp[g.U[q]] = p;
+      uint64_t s = 0;
+      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        int64_t x = g.U[q];
+        int64_t px = slot_of(&g, u, x);
+        uint64_t k4t = 0;
+        for (int64_t r = g.uoff[px]; r < g.uoff[px + 1]; ++r) k4t += (stamp[g.U[r]] == p);
+        s += k4t;
+        if (v < x) S[S_N20] = add(S[S_N20], ch2(k4t));       /* each triangle once: N20 (Thm 10) */
+      }
+      K4e[p] = s / 2;
+      K4e[g.rev[p]] = s / 2;
+    }
+  for (int64_t v = 0; v <= n; ++v) stamp[v] = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t s = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += K4e[p];
+    K4i[i] = s / 3;
+    S[S_K4] = add(S[S_K4], K4i[i]);
+  }
+  S[S_K4] /= 4;
+
+  /* ---- per-triangle sums N10, N16 (Thm 10) and the directed tailed-triangle
+   * correction of the 5-cycle count: each triangle once (u < v < x by id) ---- */
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+      int64_t v = col[p];
+      if (v <= u) continue;
+      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        int64_t x = g.U[q];
+        if (x <= v) continue;
+        int64_t vs[3] = {u, v, x};
+        uint64_t T_uv = TE(p), T_ux = TE(slot_of(&g, u, x)), T_vx = TE(slot_of(&g, v, x));
+        /* edge opposite vertex k: k = x -> (u,v), k = v -> (u,x), k = u -> (v,x) */
+        uint64_t Topp[3] = {T_vx, T_ux, T_uv};
+        for (int k = 0; k < 3; ++k) {
+          uint64_t dk = (uint64_t)g.deg[vs[k]];
+          S[S_N10A] = add(S[S_N10A], mul(Topp[k] - 1, dk - 2));
+        }
+        /* shared vertex i: the two triangle edges at i */
+        S[S_N16A] = add(S[S_N16A], mul(T_uv - 1, T_ux - 1));   /* at u */
+        S[S_N16A] = add(S[S_N16A], mul(T_uv - 1, T_vx - 1));   /* at v */
+        S[S_N16A] = add(S[S_N16A], mul(T_ux - 1, T_vx - 1));   /* at x */
+      }
+    }
+
+  /* ---- 4-cycles per vertex and per edge from the pair counts
+   * W(i, j) = |N(i) cap N(j)| (two-hop from each i):
+   *   C4(i)      = sum_{j != i} C(W(i,j), 2)
+   *   C4((i,k))  = sum_{j in N(k), j != i} (W(i,j) - 1)
+   * and, on the same pass, N13 = sum_{i<j} C(W(i,j), 3) and
+   * N17 = sum_{i<j} (W(i,j) - 2) cc(i,j) with cc(i,j) the number of edges
+   * inside N(i) cap N(j) (Thm 11), gathered from the triangles at i. ---- */
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t nt = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t c = col[p];
+      for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
+        int64_t j = col[q];
+        if (j == i) continue;
+        if (stamp[j] != i) { stamp[j] = i; cnt[j] = 0; cc[j] = 0; touched[nt++] = j; }
+        cnt[j]++;
+      }
+    }
+    /* diamonds with tip i: triangle (i, x, y), x < y, and j in N(x) cap N(y), j != i */
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t x = col[p];
+      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        int64_t y = g.U[q];
+        if (y <= x) continue;
+        int64_t pxy = slot_of(&g, x, y);
+        for (int64_t r = g.uoff[pxy]; r < g.uoff[pxy + 1]; ++r) {
+          int64_t j = g.U[r];
+          if (j != i) cc[j]++;
+        }
+      }
+    }
+    u128 c4 = 0;
+    for (int64_t a = 0; a < nt; ++a) {
+      int64_t j = touched[a];
+      c4 = add(c4, ch2((uint64_t)cnt[j]));
+      if (j > i) {
+        S[S_N13] = add(S[S_N13], ch3((uint64_t)cnt[j]));
+        if (cc[j]) S[S_N17] = add(S[S_N17], mul((uint64_t)(cnt[j] - 2), (uint64_t)cc[j]));
+      }
+    }
+    C4i[i] = (uint64_t)c4;
+    if (c4 >> 64) g_ovf = 1;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t k = col[p];
+      uint64_t s = 0;
+      for (int64_t q = rp[k]; q < rp[k + 1]; ++q) {
+        int64_t j = col[q];
+        if (j != i) s += (uint64_t)(cnt[j] - 1);
+      }
+      C4e[p] = s;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) S[S_C4] = add(S[S_C4], C4i[i]);
+  S[S_C4] /= 4;
+
+  /* ---- vertex- and edge-cut sums using C4 and K4 (Thms 8, 9) ---- */
+  for (int64_t i = 0; i < n; ++i) {
+    if (C4i[i]) S[S_N7A] = add(S[S_N7A], mul(C4i[i], (uint64_t)g.deg[i] - 2));
+    if (K4i[i]) S[S_N15] = add(S[S_N15], mul(K4i[i], (uint64_t)g.deg[i] - 3));
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (col[p] <= i) continue;
+      uint64_t te = TE(p);
+      S[S_N12A] = add(S[S_N12A], mul(C4e[p], te));
+      if (K4e[p]) S[S_N19] = add(S[S_N19], mul(K4e[p], te - 2));
+    }
+
+  /* ---- wheels (N18): the number of 4-cycles in the graph induced on N(c),
+   * summed over centres c.  For u in N(c) the two-hop count inside G[N(c)]
+   * reaches v through k in N(c) cap N(u) = U(c,u) and v in U(c,k); every
+   * 4-cycle is reached from each of its 4 vertices, so the sum of C(., 2)
+   * over ordered (u, v) is 4 x N18 (Thm 11). ---- */
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t p = rp[c]; p < rp[c + 1]; ++p) pos[col[p]] = p;   /* slot of (c -> x) */
+    for (int64_t p = rp[c]; p < rp[c + 1]; ++p) {
+      int64_t u = col[p], nt = 0;
+      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        int64_t k = g.U[q];
+        int64_t pk = pos[k];
+        for (int64_t r = g.uoff[pk]; r < g.uoff[pk + 1]; ++r) {
+          int64_t v = g.U[r];
+          if (v == u) continue;
+          if (stamp2[v] != p) { stamp2[v] = p; cnt[v] = 0; touched[nt++] = v; }
+          cnt[v]++;
+        }
+      }
+      for (int64_t a = 0; a < nt; ++a) S[S_N18X4] = add(S[S_N18X4], ch2((uint64_t)cnt[touched[a]]));
+    }
+  }
+
+  /* ---- 5-cycles (Thm 13).  For every directed 3-path i <- a -> b -> j of the
+   * degree-ordered DAG (a < i, a < b < j, b != i, j != i), count the vertices
+   * c in N(i) cap N(j), c != a, b, with c < max(i, j) (out-wedges and in-out
+   * wedges between i and j in either direction):
+   *   sum over paths of w'(i, j)             (the product term)
+   *   minus sum over paths of [a~j] + [b~i] (paths whose own vertex is
+   *                                           counted by w': the directed
+   *                                           tailed triangles Z).
+   * The degree order has three acyclic 5-cycle types up to isomorphism; each
+   * 5-cycle is met exactly once this way. ---- */
+  /* out-lists of the degree-ordered DAG: N+(v) = {u in N(v) : v < u} */
+  outp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  outc = (int32_t*)malloc(sizeof(int32_t) * (nnz / 2 + 1));
+  stamp3 = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  if (!outp || !outc || !stamp3) { rc = ORACLE_ENOMEM; goto done; }
+  outp[0] = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t w = outp[v];
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p)
+      if (prec(&g, v, col[p])) outc[w++] = col[p];
+    outp[v + 1] = w;
+  }
+  for (int64_t v = 0; v <= n; ++v) stamp3[v] = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t nt = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t c = col[p];
+      for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
+        int64_t j = col[q];
+        if (j == i) continue;
+        int64_t top = prec(&g, i, j) ? j : i;
+        if (!prec(&g, c, top)) continue;
+        if (stamp[j] != -2 - i) { stamp[j] = -2 - i; wp[j] = 0; touched[nt++] = j; }
+        wp[j]++;
+      }
+    }
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) stamp2[col[p]] = -2 - i;   /* N(i) marker */
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t a = col[p];
+      if (!prec(&g, a, i)) continue;
+      for (int64_t q = rp[a]; q < rp[a + 1]; ++q) stamp3[col[q]] = p;       /* N(a) marker */
+      for (int64_t q = outp[a]; q < outp[a + 1]; ++q) {
+        int64_t b = outc[q];
+        if (b == i) continue;
+        uint64_t b_adj_i = (stamp2[b] == -2 - i);
+        for (int64_t r = outp[b]; r < outp[b + 1]; ++r) {
+          int64_t j = outc[r];
+          if (j == i) continue;
+          uint64_t w = (stamp[j] == -2 - i) ? (uint64_t)wp[j] : 0;
+          S[S_N8M] = add(S[S_N8M], w);
+          S[S_N8Z] = add(S[S_N8Z], (uint64_t)(stamp3[j] == p) + b_adj_i);
+        }
+      }
+    }
+  }
+
+  /* ---- 5-cliques (Thm 14): every K5 contains exactly one directed
+   * bipyramid whose triangle (i < j < k) is its three lowest vertices; count
+   * adjacent pairs inside L = N+(i) cap N+(j) cap N+(k). ---- */
+  for (int64_t v = 0; v <= n; ++v) { stamp[v] = -1; stamp2[v] = -1; }
+  {
+    int64_t tag = 0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t j = col[p];
+        if (!prec(&g, i, j)) continue;
+        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+          int64_t k = g.U[q];
+          if (!prec(&g, j, k)) continue;
+          ++tag;
+          for (int64_t r = outp[k]; r < outp[k + 1]; ++r) stamp[outc[r]] = tag;   /* N+(k) */
+          int64_t nl = 0;
+          for (int64_t r = g.uoff[p]; r < g.uoff[p + 1]; ++r) {
+            int64_t l = g.U[r];
+            if (stamp[l] == tag) { touched[nl++] = l; stamp2[l] = tag; }        /* l in L */
+          }
+          for (int64_t a2 = 0; a2 < nl; ++a2) {
+            int64_t l = touched[a2];
+            for (int64_t r = outp[l]; r < outp[l + 1]; ++r)
+              if (stamp2[outc[r]] == tag) S[S_N21] = add(S[S_N21], 1);          /* l -> l' inside L */
+          }
+        }
+      }
+  }
+
+  /* ---- terms of the disconnected patterns (Thm 3, App. A) ---- */
+  S[S_WM] = mul(S[S_W], S[S_M]);
+  S[S_TM] = mul(S[S_T], S[S_M]);
+  for (int64_t c = 0; c < n; ++c) {
+    uint64_t dc = (uint64_t)g.deg[c];
+    S[S_D2D] = add(S[S_D2D], mul(ch2(dc), dc));
+    u128 nb = 0;
+    for (int64_t p = rp[c]; p < rp[c + 1]; ++p) nb = add(nb, (uint64_t)g.deg[col[p]]);
+    if (dc) S[S_DNBR] = add(S[S_DNBR], mul(dc - 1, nb));
+    S[S_TD] = add(S[S_TD], mul(t[c], dc));
+  }
+
+  for (int s = 0; s < S_COUNT; ++s) {
+    sums[2 * s] = (uint64_t)S[s];
+    sums[2 * s + 1] = (uint64_t)(S[s] >> 64);
+  }
+  for (int64_t p = 0; p < nnz; ++p) {
+    if (Te_out) Te_out[p] = TE(p);
+    if (C4e_out) C4e_out[p] = C4e[p];
+    if (K4e_out) K4e_out[p] = K4e[p];
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    if (ti_out) ti_out[v] = t[v];
+    if (C4i_out) C4i_out[v] = C4i[v];
+    if (K4i_out) K4i_out[v] = K4i[v];
+  }
+  rc = g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
+done:
+  free(t); free(C4e); free(C4i); free(K4e); free(K4i); free(cnt); free(cc); free(wp);
+  free(stamp); free(stamp2); free(touched); free(pos); free(outp); free(outc); free(stamp3);
+  free_g(&g);
+  return rc;
+}

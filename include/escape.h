@@ -1,0 +1,146 @@
+/*
+ * escape.h -- C ABI of the GB300 ESCAPE census library (libescape_gb300.so).
+ *
+ * The library computes the exact census of all 3-, 4- and 5-vertex patterns of
+ * an undirected simple graph: for every isomorphism class H of k-vertex graphs
+ * (k = 3, 4, 5) the induced count C_H = #{S : |S| = k, G[S] ~ H} and the
+ * non-induced count N_H (Sec. 3.1 of Pinar, Seshadhri, Vishal, "ESCAPE:
+ * Efficiently Counting All 5-Vertex Subgraphs", arXiv 1610.09411).  Every step
+ * runs on the GPU: degree ordering (Sec. 3.2), per-vertex/per-edge triangle,
+ * 4-cycle and 4-clique counts (Thms 5-7), the pattern-cutting closed forms
+ * (Thms 4, 8-11), 5-cycles and 5-cliques (Thms 13-14), disconnected patterns
+ * (Thm 3) and the induced/non-induced conversion (App. B).
+ *
+ * Class order.  3-vertex: empty, edge, wedge, triangle.  4-vertex: the six
+ * connected patterns of the paper's 4-vertex figure (3-star, 3-path, tailed
+ * triangle, 4-cycle, diamond, 4-clique), then independent set, edge + 2
+ * isolated, 2 disjoint edges, wedge + isolated, triangle + isolated.
+ * 5-vertex: patterns 1-21 of the paper's figure of connected 5-vertex patterns,
+ * 22-32 of its figure of disconnected 5-vertex patterns (empty, edge, 2 edges,
+ * wedge, triangle, 3-star, 3-path, tailed triangle, 4-cycle, diamond, 4-clique,
+ * each plus isolated vertices), 33 = wedge + disjoint edge, 34 = triangle +
+ * disjoint edge (the two classes the paper's figure leaves out).
+ *
+ * Counts are exact unsigned 128-bit integers (two little-endian 64-bit words).
+ *
+ * Threading: a handle may be used by one thread at a time.  All calls are
+ * synchronous with respect to the host: they enqueue work on the given CUDA
+ * stream (NULL = the legacy default stream) and wait for it before returning.
+ * No C++ exception or exit() crosses this boundary.
+ */
+#ifndef ESCAPE_GB300_H
+#define ESCAPE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct escape_graph escape_graph;   /* opaque; owns a device copy of the CSR */
+
+typedef struct { uint64_t lo, hi; } escape_u128;
+
+typedef struct {
+  escape_u128 c3[4], c4[11], c5[34];   /* induced counts, class order above       */
+  escape_u128 n3[4], n4[11], n5[34];   /* non-induced counts (Sec. 3.1)             */
+} escape_census;
+
+typedef enum {
+  ESCAPE_OK = 0,
+  ESCAPE_EINVAL = 1,     /* invalid argument or malformed graph                     */
+  ESCAPE_ENOMEM = 2,     /* a host or device allocation failed                      */
+  ESCAPE_ECUDA = 3,      /* a CUDA call failed (the context may be unusable)        */
+  ESCAPE_EOVERFLOW = 4,  /* a size exceeds what the library supports                */
+  ESCAPE_ETIMEOUT = 5,   /* a bounded device wait ran out                           */
+  ESCAPE_EINTERNAL = 6   /* a device-side consistency check failed                  */
+} escape_status;
+
+/* flags for escape_load_csr / escape_census5_batch */
+#define ESCAPE_HOST_PTRS   0u        /* row_ptr/col are host memory                    */
+#define ESCAPE_DEVICE_PTRS 1u        /* row_ptr/col are device memory                  */
+#define ESCAPE_NORMALIZE   2u        /* symmetrise, drop duplicates and self-loops (Sec. 8) */
+
+/*
+ * escape_load_csr -- copy a graph to the device and validate it.
+ *   n        number of vertices, 0 <= n <= 2^31 - 1
+ *   nnz      number of entries of col (= 2 x edges for a simple symmetric graph)
+ *   row_ptr  int64[n + 1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz
+ *   col      int32[nnz], neighbour ids in [0, n)
+ *   flags    ESCAPE_HOST_PTRS or ESCAPE_DEVICE_PTRS, optionally | ESCAPE_NORMALIZE.
+ *            Without NORMALIZE the input must already be simple: rows sorted
+ *            strictly ascending, no self-loops, symmetric; otherwise EINVAL.
+ *            With NORMALIZE any entries are accepted (direction ignored,
+ *            duplicates and self-loops dropped); ids out of range give EINVAL.
+ *   stream   cudaStream_t as void* (NULL = default stream)
+ *   out      receives the new handle; untouched on error.
+ * The caller keeps ownership of row_ptr/col (they are copied and may be freed
+ * on return).  The handle is freed with escape_free.
+ */
+escape_status escape_load_csr(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col, uint32_t flags,
+                              void* stream, escape_graph** out);
+
+/* Vertices and undirected edges of a loaded graph (either pointer may be NULL). */
+escape_status escape_graph_info(const escape_graph* g, int64_t* n, int64_t* m);
+
+/*
+ * escape_census5 -- the full census of a loaded graph (Thm 2: all connected
+ * 5-vertex patterns; Thm 3: disconnected ones; App. B: induced counts),
+ * together with the 3- and 4-vertex census (Thm 1).
+ *   out      host memory; written only on success.
+ * Device work space is allocated for the call and freed before it returns.
+ * Graphs with n < 5, no edges, or no triangles are valid.
+ */
+escape_status escape_census5(escape_graph* g, escape_census* out, void* stream);
+
+/*
+ * escape_census5_batch -- census of many small graphs given as one block
+ * diagonal CSR.
+ *   num_graphs   G >= 0
+ *   vtx_offsets  int64[G + 1]: graph k owns global rows vtx_offsets[k] ..
+ *                vtx_offsets[k+1]-1; vtx_offsets[0] = 0
+ *   row_ptr      int64[vtx_offsets[G] + 1] over all rows
+ *   col          int32[row_ptr[last]]: neighbour ids LOCAL to each graph
+ *                (0 .. n_k - 1)
+ *   flags        as for escape_load_csr (pointers are host or device memory)
+ *   out          host array of G results, written only on success.
+ * Results are identical to calling escape_census5 on each graph alone.
+ */
+escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offsets, const int64_t* row_ptr,
+                                   const int32_t* col, uint32_t flags, escape_census* out, void* stream);
+
+/*
+ * escape_per_element -- per-vertex and per-edge counts of the last
+ * escape_census5 call on this handle (Thm 7), in the layout of the loaded CSR:
+ *   tri_e, c4_e, k4_e   uint64[nnz]: triangles / 4-cycles / 4-cliques through
+ *                       the edge of each CSR entry (both entries of an edge agree)
+ *   tri_v, c4_v, k4_v   uint64[n]: triangles / 4-cycles / 4-cliques at each vertex
+ * Host memory; any pointer may be NULL.  EINVAL if no census has been run
+ * with per-element output enabled (escape_set_options).
+ */
+escape_status escape_per_element(escape_graph* g, uint64_t* tri_e, uint64_t* c4_e, uint64_t* k4_e, uint64_t* tri_v,
+                                 uint64_t* c4_v, uint64_t* k4_v, void* stream);
+
+/* Options: keep_per_element (0/1) makes escape_census5 retain the arrays
+ * read by escape_per_element; cta_per_sm sets the persistent-CTA count of the
+ * sweep kernels (0 = default). */
+escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_per_sm);
+
+/*
+ * escape_last_phase_ms -- device time (CUDA events) of each phase of the last
+ * escape_census5 call on this handle: [0] orientation, [1] triangles,
+ * [2] cliques and per-triangle sums, [3] 4-cycles, [4] common-neighbour lists,
+ * [5] pair sweep (N13, N17), [6] wheels (N18), [7] 5-cycles, [8] assembly.
+ * Writes min(count, 9) floats; returns the number of phases available.
+ */
+int escape_last_phase_ms(const escape_graph* g, float* ms, int count);
+
+void escape_free(escape_graph* g);
+
+/* Static string for a status code. */
+const char* escape_status_str(escape_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESCAPE_GB300_H */

@@ -77,6 +77,10 @@ def _load():
             lib.oracle_classify.argtypes = [c_int, c_int]
             lib.oracle_census_sums.restype = c_int
             lib.oracle_census_sums.argtypes = [i64, P, P, P, P, P, P, P, P, P]
+            lib.oracle_edge_elements.restype = c_int
+            lib.oracle_edge_elements.argtypes = [i64, P, P, i64, P, P, P, P, P]
+            lib.oracle_vertex_elements.restype = c_int
+            lib.oracle_vertex_elements.argtypes = [i64, P, P, i64, P, P, P]
             lib.oracle_num_sums.restype = c_int
             assert lib.oracle_num_sums() == len(SUM_NAMES)
             _lib = lib
@@ -245,3 +249,33 @@ def census(g, per_element: bool = False) -> dict:
     if arrs is not None:
         out["per_element"] = arrs
     return out
+
+
+def edge_elements(g, us, vs) -> dict:
+    """T, K4 and C4 of the given edges (u, v), each from its definition."""
+    rp, col = _csr(g)
+    us = np.ascontiguousarray(np.asarray(us, dtype=np.int64))
+    vs = np.ascontiguousarray(np.asarray(vs, dtype=np.int64))
+    k = us.size
+    T = np.zeros(max(k, 1), dtype=np.uint64)
+    K4 = np.zeros(max(k, 1), dtype=np.uint64)
+    C4 = np.zeros(max(k, 1), dtype=np.uint64)
+    rc = _load().oracle_edge_elements(g.n, rp.ctypes.data, col.ctypes.data, k, us.ctypes.data, vs.ctypes.data,
+                                      T.ctypes.data, K4.ctypes.data, C4.ctypes.data)
+    if rc:
+        raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
+    return {"T_e": T[:k], "K4_e": K4[:k], "C4_e": C4[:k]}
+
+
+def vertex_elements(g, vs) -> dict:
+    """t and C4 of the given vertices, each from its definition."""
+    rp, col = _csr(g)
+    vs = np.ascontiguousarray(np.asarray(vs, dtype=np.int64))
+    k = vs.size
+    t = np.zeros(max(k, 1), dtype=np.uint64)
+    C4 = np.zeros(max(k, 1), dtype=np.uint64)
+    rc = _load().oracle_vertex_elements(g.n, rp.ctypes.data, col.ctypes.data, k, vs.ctypes.data,
+                                        t.ctypes.data, C4.ctypes.data)
+    if rc:
+        raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
+    return {"t_i": t[:k], "C4_i": C4[:k]}

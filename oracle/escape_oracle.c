@@ -705,3 +705,90 @@ done:
   free_g(&g);
   return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* Single-element values from their definitions (for sampled checks of */
+/* graphs too large for the whole census above):                      */
+/*   T(u,v)   = |N(u) cap N(v)|                                        */
+/*   K4(u,v)  = number of edges inside N(u) cap N(v)                   */
+/*   C4(u,v)  = sum_{j in N(v), j != u} (|N(u) cap N(j)| - 1)          */
+/*   t(i)     = (1/2) sum_{v in N(i)} T(i,v)                           */
+/*   C4(i)    = sum_{j != i} C(|N(i) cap N(j)|, 2)                     */
+/* ------------------------------------------------------------------ */
+static int64_t* two_hop(int64_t n, const int64_t* rp, const int32_t* col, int64_t u,
+                        int64_t* cnt, int64_t* touched) {
+  int64_t nt = 0;
+  for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+    int64_t c = col[p];
+    for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
+      int64_t j = col[q];
+      if (j == u) continue;
+      if (cnt[j] == 0) touched[nt++] = j;
+      cnt[j]++;
+    }
+  }
+  touched[n] = nt;   /* count kept in the spare last slot */
+  return touched;
+}
+
+int oracle_edge_elements(int64_t n, const int64_t* rp, const int32_t* col, int64_t count,
+                         const int64_t* us, const int64_t* vs, uint64_t* T, uint64_t* K4, uint64_t* C4) {
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* touched = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  if (!cnt || !touched || !mark) { free(cnt); free(touched); free(mark); return ORACLE_ENOMEM; }
+  for (int64_t v = 0; v <= n; ++v) mark[v] = -1;
+  for (int64_t s = 0; s < count; ++s) {
+    int64_t u = us[s], v = vs[s];
+    if (u < 0 || u >= n || v < 0 || v >= n || !has_edge(rp, col, u, v)) { free(cnt); free(touched); free(mark); return ORACLE_EINVAL; }
+    /* common neighbours, marked */
+    uint64_t t = 0;
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p)
+      if (has_edge(rp, col, v, col[p])) { mark[col[p]] = s; ++t; }
+    T[s] = t;
+    uint64_t k = 0;
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+      int64_t x = col[p];
+      if (mark[x] != s) continue;
+      for (int64_t q = rp[x]; q < rp[x + 1]; ++q) k += (mark[col[q]] == s);
+    }
+    K4[s] = k / 2;
+    two_hop(n, rp, col, u, cnt, touched);
+    uint64_t c = 0;
+    for (int64_t q = rp[v]; q < rp[v + 1]; ++q) {
+      int64_t j = col[q];
+      if (j != u) c += (uint64_t)(cnt[j] - 1);
+    }
+    C4[s] = c;
+    for (int64_t a = 0; a < touched[n]; ++a) cnt[touched[a]] = 0;
+  }
+  free(cnt); free(touched); free(mark);
+  return ORACLE_OK;
+}
+
+int oracle_vertex_elements(int64_t n, const int64_t* rp, const int32_t* col, int64_t count,
+                           const int64_t* vs, uint64_t* t_out, uint64_t* C4_out) {
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* touched = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  if (!cnt || !touched) { free(cnt); free(touched); return ORACLE_ENOMEM; }
+  for (int64_t s = 0; s < count; ++s) {
+    int64_t i = vs[s];
+    if (i < 0 || i >= n) { free(cnt); free(touched); return ORACLE_EINVAL; }
+    uint64_t tt = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t v = col[p];
+      tt += (uint64_t)merge_count(col + rp[i], rp[i + 1] - rp[i], col + rp[v], rp[v + 1] - rp[v]);
+    }
+    t_out[s] = tt / 2;
+    two_hop(n, rp, col, i, cnt, touched);
+    uint64_t c = 0;
+    for (int64_t a = 0; a < touched[n]; ++a) {
+      uint64_t w = (uint64_t)cnt[touched[a]];
+      c += w * (w - 1) / 2;
+      cnt[touched[a]] = 0;
+    }
+    C4_out[s] = c;
+  }
+  free(cnt); free(touched);
+  return ORACLE_OK;
+}

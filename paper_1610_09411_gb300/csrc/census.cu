@@ -1,0 +1,1193 @@
+// census.cu -- the enumeration and assembly kernels of the 5-vertex census.
+//
+// All vertices are ranks of the degree order (Sec. 3.2), so `a < b` is the
+// order itself; N+(v) is the suffix of row v, N-(v) its prefix.  Counts are
+// exact: per-element counters are 32/64-bit, global sums 128-bit.
+//
+// Kernel map (paper section -> kernel):
+//   Thm 4, 8, 9 degree/edge closed forms ...... k_vertex_basic, k_edge_sums
+//   Thm 7 triangles T(e), t(i) ................ k_tri_small / k_tri_large (pass A)
+//   Thm 6/7 4-cliques K4(e), K4(t); Thm 10 N10,
+//     N16, N20; Thm 14 5-cliques; Thm 13's
+//     directed tailed triangles ................ k_clique_small / k_clique_large (pass B)
+//   Thm 5 4-cycles C4(e), C4(i) ................ k_cycles4
+//   Thm 11/12 N13, N17 (pairs and diamonds) .... k_pairs
+//   Thm 11 N18 (wheels) ........................ k_wheels
+//   Thm 13 5-cycles ............................ k_cycles5
+//   Thm 3 + App. B assembly .................... k_assemble
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+namespace esc {
+
+// ----------------------------------------------------------------------------
+// Small device hash set of vertex ranks -> position (open addressing).
+// ----------------------------------------------------------------------------
+struct PosHash {
+  int32_t* keys;     // EMPTY = -1
+  int32_t* vals;
+  int mask;
+  __device__ __forceinline__ uint32_t h(int32_t k) const { return ((uint32_t)k * 0x9E3779B1u) >> 7; }
+  __device__ __forceinline__ void insert(int32_t k, int32_t v) {
+    uint32_t s = h(k) & mask;
+    while (true) {
+      int32_t old = atomicCAS(&keys[s], -1, k);
+      if (old == -1 || old == k) { vals[s] = v; return; }
+      s = (s + 1) & mask;
+    }
+  }
+  __device__ __forceinline__ int32_t find(int32_t k) const {
+    uint32_t s = h(k) & mask;
+    while (true) {
+      int32_t kk = keys[s];
+      if (kk == k) return vals[s];
+      if (kk == -1) return -1;
+      s = (s + 1) & mask;
+    }
+  }
+};
+
+static __host__ __device__ __forceinline__ int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// ============================================================================
+// Degree sums (Thm 4, Thm 8 N1/N3, Thm 9 N2, App. A P3+K2 terms).
+// One warp per vertex.
+// ============================================================================
+__global__ void k_vertex_basic(DevGraph g, Acc128* acc) {
+  __shared__ u128 sh[32];
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  LocalAcc<8> la;
+  la.zero();
+  for (int64_t v = warp; v < g.n; v += nwarps) {
+    unsigned long long dv = (unsigned long long)dg_deg(g, v);
+    u128 s1 = 0, s2 = 0, nb = 0, n2a = 0, p4a = 0;
+    for (int64_t p = g.R[v] + lane; p < g.R[v + 1]; p += 32) {
+      int32_t a = g.C[p];
+      unsigned long long da = (unsigned long long)dg_deg(g, a);
+      s1 += da - 1;
+      s2 += (u128)(da - 1) * (da - 1);
+      nb += da;
+      n2a += ch2(dv - 1) * (da - 1);
+      if (a > v) p4a += (u128)(dv - 1) * (da - 1);
+    }
+    s1 = warp_sum_u128(s1);
+    s2 = warp_sum_u128(s2);
+    nb = warp_sum_u128(nb);
+    n2a = warp_sum_u128(n2a);
+    p4a = warp_sum_u128(p4a);
+    if (lane == 0) {
+      la.v[0] += ch2(dv);
+      la.v[1] += ch3(dv);
+      la.v[2] += ch4(dv);
+      la.v[3] += ch2(dv) * dv;
+      la.v[4] += dv ? (u128)(dv - 1) * nb : 0;
+      la.v[5] += n2a;
+      la.v[6] += (s1 * s1 - s2) / 2;
+      la.v[7] += p4a;
+    }
+  }
+  const int ids[8] = {ACC_W, ACC_S3, ACC_S4, ACC_D2D, ACC_DNBR, ACC_N2A, ACC_N3A, ACC_P4A};
+  flush_acc(la, ids, acc, sh);
+}
+
+// ============================================================================
+// Pass A: triangles.  Every triangle x < v < w is found once from its lowest
+// vertex x as v in N+(x), w in N+(v) cap N+(x) (Thm 7).  It adds one to the
+// triangle counts of its three edges (canonical slots in the lower endpoint's
+// out-list) and contributes d+(x) + d+(v) + d+(w) - 3 to the directed
+// tailed-triangle term of the 5-cycle count (Thm 13).
+// ============================================================================
+static constexpr int SMALL_DPLUS = 32;    // warp-per-vertex path up to this out-degree
+
+// Warp per vertex with d+ <= 32: N+(x) in a per-warp shared-memory list,
+// membership by binary search.
+__global__ void k_tri_small(DevGraph g, const int32_t* items, int64_t nitems, uint32_t* T, Acc128* acc) {
+  __shared__ u128 sh[32];
+  __shared__ int32_t lst[8][SMALL_DPLUS];
+  __shared__ uint32_t cnt[8][SMALL_DPLUS];
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  LocalAcc<2> la;
+  la.zero();
+  for (int64_t it = warp; it < nitems; it += nwarps) {
+    int64_t x = items[it];
+    int64_t o = g.op[x];
+    int d = (int)(g.R[x + 1] - o);
+    if (lane < d) lst[wl][lane] = g.C[o + lane];
+    cnt[wl][lane] = 0;
+    __syncwarp();
+    unsigned long long dpx = (unsigned long long)d;
+    for (int a = 0; a < d; ++a) {
+      int32_t v = lst[wl][a];
+      int64_t vo = g.op[v], ve = g.R[v + 1];
+      unsigned long long dpv = (unsigned long long)(ve - vo);
+      for (int64_t q = vo + lane; q < ve; q += 32) {
+        int32_t w = g.C[q];
+        int lo = a + 1, hi = d;                 // w > v, so only positions after a
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (lst[wl][mid] < w) lo = mid + 1; else hi = mid; }
+        if (lo < d && lst[wl][lo] == w) {
+          atomicAdd(&T[q], 1u);
+          atomicAdd(&cnt[wl][a], 1u);
+          atomicAdd(&cnt[wl][lo], 1u);
+          la.v[0] += 1;
+          la.v[1] += dpx + dpv + (unsigned long long)(g.R[w + 1] - g.op[w]) - 3;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < d && cnt[wl][lane]) atomicAdd(&T[o + lane], cnt[wl][lane]);
+    __syncwarp();
+  }
+  const int ids[2] = {ACC_T, ACC_N8Z};
+  flush_acc(la, ids, acc, sh);
+}
+
+// CTA per vertex with d+ > 32: N+(x) in a shared-memory hash.
+__global__ void k_tri_large(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
+                            uint32_t* T, Acc128* acc, int hash_cap) {
+  extern __shared__ int32_t smem[];
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  int32_t* hk = smem;
+  int32_t* hv = hk + hash_cap;
+  uint32_t* cnt = (uint32_t*)(hv + hash_cap);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  LocalAcc<2> la;
+  la.zero();
+  while (true) {
+    int64_t it = next_item(qctr, nitems, &sh_item);
+    if (it < 0) break;
+    int64_t x = items[it];
+    int64_t o = g.op[x];
+    int d = (int)(g.R[x + 1] - o);
+    int hsz = pow2_at_least(2 * d);
+    PosHash H{hk, hv, hsz - 1};
+    for (int i = threadIdx.x; i < hsz; i += blockDim.x) hk[i] = -1;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) H.insert(g.C[o + i], i);
+    __syncthreads();
+    unsigned long long dpx = (unsigned long long)d;
+    for (int a = wid; a < d; a += nw) {
+      int32_t v = g.C[o + a];
+      int64_t vo = g.op[v], ve = g.R[v + 1];
+      unsigned long long dpv = (unsigned long long)(ve - vo);
+      unsigned on_xv = 0;
+      for (int64_t q = vo + lane; q < ve; q += 32) {
+        int32_t w = g.C[q];
+        int b = H.find(w);
+        if (b >= 0) {
+          atomicAdd(&T[q], 1u);
+          atomicAdd(&cnt[b], 1u);
+          on_xv += 1;
+          la.v[0] += 1;
+          la.v[1] += dpx + dpv + (unsigned long long)(g.R[w + 1] - g.op[w]) - 3;
+        }
+      }
+      on_xv = (unsigned)warp_sum_u64(on_xv);
+      if (lane == 0 && on_xv) atomicAdd(&cnt[a], on_xv);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+      if (cnt[i]) atomicAdd(&T[o + i], cnt[i]);
+    __syncthreads();
+  }
+  const int ids[2] = {ACC_T, ACC_N8Z};
+  flush_acc(la, ids, acc, sh);
+}
+
+// Copy canonical per-edge values to the reverse slot; per-vertex sums.
+__global__ void k_sym_T(DevGraph g, uint32_t* T, unsigned long long* tv) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps)
+    for (int64_t p = g.op[v] + lane; p < g.R[v + 1]; p += 32) T[g.rev[p]] = T[p];
+}
+
+__global__ void k_vertex_from_edges_T(DevGraph g, const uint32_t* T, unsigned long long* tv) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps) {
+    unsigned long long s = 0;
+    for (int64_t p = g.R[v] + lane; p < g.R[v + 1]; p += 32) s += T[p];
+    s = warp_sum_u64(s);
+    if (lane == 0) tv[v] = s / 2;
+  }
+}
+
+__global__ void k_sym_u64(DevGraph g, unsigned long long* E) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps)
+    for (int64_t p = g.op[v] + lane; p < g.R[v + 1]; p += 32) E[g.rev[p]] = E[p];
+}
+
+// 4-cycle per-edge counts arrive in either slot of an edge: fold them.
+__global__ void k_fold_u64(DevGraph g, unsigned long long* E) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps)
+    for (int64_t p = g.op[v] + lane; p < g.R[v + 1]; p += 32) {
+      int64_t r = g.rev[p];
+      unsigned long long s = E[p] + E[r];
+      E[p] = s;
+      E[r] = s;
+    }
+}
+
+__global__ void k_vertex_sum_div(DevGraph g, const unsigned long long* E, unsigned long long* V, unsigned div) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps) {
+    unsigned long long s = 0;
+    for (int64_t p = g.R[v] + lane; p < g.R[v + 1]; p += 32) s += E[p];
+    s = warp_sum_u64(s);
+    if (lane == 0) V[v] = s / div;
+  }
+}
+
+// ============================================================================
+// Pass B: 4-cliques, 5-cliques and the per-triangle sums.
+//
+// For the lowest vertex x, B holds the adjacency bit matrix of the graph
+// induced on N+(x) (row a = the out-neighbours of N+(x)[a] that are also in
+// N+(x)).  For an edge (a, b) of it -- the triangle {x, v_a, v_b} with x
+// lowest --
+//   alpha = |row_a & row_b|   apexes of the triangle above x (K4s x,a,b,c)
+//   beta  = apexes below x: in-neighbours y of x adjacent to v_a and v_b.
+//           With D_a = bit set over N-(x) of {y : v_a in N+(y)}, beta =
+//           |D_a & D_b|.
+// so K4(t) = alpha + beta (Thm 7), and
+//   N20 += C(alpha + beta, 2)                                (Thm 10)
+//   N10 += sum over the 3 vertices k of (T(opposite edge) - 1)(d_k - 2)
+//   N16 += sum over the 3 vertices of (T(e1) - 1)(T(e2) - 1)  (Thm 10)
+//   K4 total += alpha / 3; K4(v_a, v_b) += alpha; K4(x, v_a) += alpha / 2 summed
+//   K5 += |row_a & row_b & row_c| above c for every c in row_a & row_b above b
+//        (each 5-clique once, at its three lowest vertices: Thm 14)
+// ============================================================================
+struct CliqueScratch {
+  uint64_t* D;         // per CTA: d+ x ceil(d-/64) words
+  int64_t d_words;     // capacity per CTA in words
+};
+
+// B rows are symmetric (row a = every neighbour of v_a inside N+(x)).
+__device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int b, const uint64_t* Da,
+                                            const uint64_t* Db, int DW, unsigned long long& alpha_out,
+                                            unsigned long long& beta_out, unsigned long long& k5_out) {
+  const uint64_t* ra = B + (int64_t)a * W;
+  const uint64_t* rb = B + (int64_t)b * W;
+  unsigned long long alpha = 0, k5 = 0;
+  for (int w = 0; w < W; ++w) alpha += __popcll(ra[w] & rb[w]);
+  // 5-cliques with lowest vertex x and next two v_a < v_b: every c in the
+  // common neighbourhood above b, then every l adjacent to a, b, c above c
+  int w0 = (b + 1) >> 6;
+  for (int w = w0; w < W; ++w) {
+    uint64_t cm = ra[w] & rb[w];
+    if (w == w0) cm &= ~0ull << ((b + 1) & 63);
+    while (cm) {
+      int c = w * 64 + __ffsll((long long)cm) - 1;
+      cm &= cm - 1;
+      const uint64_t* rc = B + (int64_t)c * W;
+      int u0 = (c + 1) >> 6;
+      for (int u = u0; u < W; ++u) {
+        uint64_t m = ra[u] & rb[u] & rc[u];
+        if (u == u0) m &= ~0ull << ((c + 1) & 63);
+        k5 += __popcll(m);
+      }
+    }
+  }
+  unsigned long long beta = 0;
+  if (Da) for (int w = 0; w < DW; ++w) beta += __popcll(Da[w] & Db[w]);
+  alpha_out = alpha;
+  beta_out = beta;
+  k5_out = k5;
+}
+
+// Shared-memory layout for the CTA path: hash (2 x hcap ints), nb values,
+// B (d x W u64), K4 accumulators (d u64), T of x's out-edges (d u32).
+__global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
+                               const uint32_t* T, unsigned long long* K4e, Acc128* acc, CliqueScratch cs,
+                               int hash_cap, int dmax, unsigned* status) {
+  extern __shared__ uint64_t smem64[];
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  int W_cap = (dmax + 63) >> 6;
+  uint64_t* B = smem64;                                        // dmax * W_cap
+  unsigned long long* k4x = (unsigned long long*)(B + (int64_t)dmax * W_cap);   // dmax
+  int32_t* hk = (int32_t*)(k4x + dmax);                        // hash_cap
+  int32_t* hv = hk + hash_cap;                                 // hash_cap
+  uint32_t* Tx = (uint32_t*)(hv + hash_cap);                   // dmax
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint64_t* D = cs.D + (int64_t)blockIdx.x * cs.d_words;
+  LocalAcc<7> la;
+  la.zero();
+  while (true) {
+    int64_t it = next_item(qctr, nitems, &sh_item);
+    if (it < 0) break;
+    int64_t x = items[it];
+    int64_t o = g.op[x], ib = g.R[x];
+    int d = (int)(g.R[x + 1] - o);
+    int din = (int)(o - ib);
+    if (d > dmax) {     // cannot happen: items are filtered by d+ on the host side
+      if (threadIdx.x == 0) set_err(status, DEVERR_SCRATCH);
+      continue;
+    }
+    int W = (d + 63) >> 6;
+    int DW = (din + 63) >> 6;
+    bool use_beta = din > 0 && (int64_t)d * DW <= cs.d_words;
+    if (din > 0 && !use_beta && threadIdx.x == 0) set_err(status, DEVERR_SCRATCH);
+    int hsz = pow2_at_least(2 * d);
+    PosHash H{hk, hv, hsz - 1};
+    for (int i = threadIdx.x; i < hsz; i += blockDim.x) hk[i] = -1;
+    for (int i = threadIdx.x; i < d * W; i += blockDim.x) B[i] = 0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) { k4x[i] = 0; Tx[i] = T[o + i]; }
+    if (use_beta)
+      for (int64_t i = threadIdx.x; i < (int64_t)d * DW; i += blockDim.x) D[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) H.insert(g.C[o + i], i);
+    __syncthreads();
+    // build B
+    for (int a = wid; a < d; a += nw) {
+      int32_t v = g.C[o + a];
+      for (int64_t q = g.op[v] + lane; q < g.R[v + 1]; q += 32) {
+        int b = H.find(g.C[q]);
+        if (b >= 0) {
+          atomicOr((unsigned long long*)&B[a * W + (b >> 6)], 1ull << (b & 63));
+          atomicOr((unsigned long long*)&B[b * W + (a >> 6)], 1ull << (a & 63));
+        }
+      }
+    }
+    // build D: in-neighbour y (index k) sets bit k of D_a for every v_a in N+(y)
+    if (use_beta) {
+      for (int k = wid; k < din; k += nw) {
+        int32_t y = g.C[ib + k];
+        for (int64_t q = g.op[y] + lane; q < g.R[y + 1]; q += 32) {
+          int a = H.find(g.C[q]);
+          if (a >= 0) atomicOr((unsigned long long*)&D[(int64_t)a * DW + (k >> 6)], 1ull << (k & 63));
+        }
+      }
+    }
+    __syncthreads();
+    unsigned long long dx = (unsigned long long)(g.R[x + 1] - g.R[x]);
+    // edges (a, b) of G[N+(x)]: scan N+(v_a) again to get the slot of (v_a, v_b)
+    for (int a = wid; a < d; a += nw) {
+      int32_t v = g.C[o + a];
+      unsigned long long dva = (unsigned long long)(g.R[v + 1] - g.R[v]);
+      unsigned long long k4a = 0;
+      for (int64_t q = g.op[v] + lane; q < g.R[v + 1]; q += 32) {
+        int32_t w = g.C[q];
+        int b = H.find(w);
+        if (b < 0) continue;
+        unsigned long long alpha, beta, k5;
+        clique_edge(B, W, a, b, use_beta ? D + (int64_t)a * DW : nullptr, use_beta ? D + (int64_t)b * DW : nullptr,
+                    DW, alpha, beta, k5);
+        unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
+        unsigned long long tab = T[q], txa = Tx[a], txb = Tx[b];
+        la.v[0] += alpha;                                         // 3 x K4
+        la.v[1] += ch2(alpha + beta);                             // N20
+        la.v[2] += (u128)(tab - 1) * (dx - 2) + (u128)(txb - 1) * (dva - 2) + (u128)(txa - 1) * (dvb - 2);   // N10
+        la.v[3] += (u128)(txa - 1) * (txb - 1) + (u128)(txa - 1) * (tab - 1) + (u128)(txb - 1) * (tab - 1);  // N16
+        la.v[4] += k5;                                            // N21
+        if (alpha) {
+          atomicAdd(&K4e[q], alpha);
+          atomicAdd(&k4x[b], alpha);
+          k4a += alpha;
+        }
+      }
+      k4a = warp_sum_u64(k4a);
+      if (lane == 0 && k4a) atomicAdd(&k4x[a], k4a);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+      if (k4x[i]) atomicAdd(&K4e[o + i], k4x[i] / 2);
+    __syncthreads();
+  }
+  const int ids[5] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21};
+  LocalAcc<5> l5;
+  for (int i = 0; i < 5; ++i) l5.v[i] = la.v[i];
+  flush_acc(l5, ids, acc, sh);
+}
+
+// ============================================================================
+// Thm 5: 4-cycles.  For the highest vertex i and each j < i,
+// w(i,j) = |{k in N(i) cap N(j) : k < i}| (out-wedges and in-out wedges);
+// C4 = sum C(w,2).  Per element: every wedge i - k - j adds w-1 to edges
+// (i,k), (k,j) and vertex k; every j adds C(w,2) to vertices i and j.
+// CTA per i, dense per-CTA counters over j with a touched list.
+// ============================================================================
+struct SweepScratch {
+  uint32_t* cnt;       // per CTA: n counters (kept zero between items)
+  int32_t* touched;    // per CTA: n entries
+  uint32_t* cnt2;      // second counter array (5-cycles)
+  int32_t* touched2;
+  unsigned* ntouched;  // per CTA: 2 counters
+  int64_t n;
+};
+
+__global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss, unsigned long long* C4raw,
+                          unsigned long long* C4v, Acc128* acc) {
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
+  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
+  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 c4sum = 0;
+  while (true) {
+    int64_t it = next_item(qctr, g.n, &sh_item);
+    if (it < 0) break;
+    int64_t i = g.n - 1 - it;
+    int64_t b0 = g.R[i], e0 = g.op[i];
+    if (e0 == b0) continue;           // no lower neighbours
+    if (threadIdx.x == 0) *nt = 0;
+    __syncthreads();
+    // pass 1: wedge counts
+    for (int64_t p = b0 + wid; p < e0; p += nw) {
+      int32_t k = g.C[p];
+      int64_t kb = g.R[k], ke = g.rev[p];       // N(k) below i
+      for (int64_t q = kb + lane; q < ke; q += 32) {
+        int32_t j = g.C[q];
+        if (atomicAdd(&w[j], 1u) == 0) tl[atomicAdd(nt, 1u)] = j;
+      }
+    }
+    __syncthreads();
+    unsigned ntc = *nt;
+    u128 mine = 0;
+    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) {
+      int32_t j = tl[t];
+      u128 c = ch2(w[j]);
+      if (c) { atomicAdd(&C4v[j], (unsigned long long)c); mine += c; }
+    }
+    u128 tot = block_sum_u128(mine, sh);
+    if (threadIdx.x == 0) {
+      if (tot) atomicAdd(&C4v[i], (unsigned long long)tot);
+      c4sum += tot;
+    }
+    // pass 3: per-edge counts
+    for (int64_t p = b0 + wid; p < e0; p += nw) {
+      int32_t k = g.C[p];
+      int64_t kb = g.R[k], ke = g.rev[p];
+      unsigned long long sk = 0;
+      for (int64_t q = kb + lane; q < ke; q += 32) {
+        int32_t j = g.C[q];
+        unsigned long long c = w[j] - 1;
+        if (c) { atomicAdd(&C4raw[q], c); sk += c; }
+      }
+      sk = warp_sum_u64(sk);
+      if (lane == 0 && sk) { atomicAdd(&C4raw[p], sk); atomicAdd(&C4v[k], sk); }
+    }
+    __syncthreads();
+    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) acc_add(acc, ACC_C4, c4sum);
+}
+
+// ============================================================================
+// Thm 11/12: N13 = sum_{j<i} C(W(i,j), 3) and
+// N17 = sum_{j<i} (W(i,j) - 2) cc(i,j), cc = edges inside N(i) cap N(j).
+// W(i,.) from every wedge i - c - j (c in N(i), j in N(c), j < i); the cc
+// term is gathered per diamond: for each triangle {i, x, y} (x < y) and each
+// j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
+// per-edge triangle lists).
+// ============================================================================
+struct TriLists {
+  const int64_t* off;   // per slot: start of the edge's common-neighbour list (both slots)
+  const int32_t* U;     // sorted common neighbours
+};
+
+__device__ __forceinline__ int64_t find_slot(const DevGraph& g, int64_t u, int32_t v) {
+  int64_t q = lower_bound_i32(g.C, g.R[u], g.R[u + 1], v);
+  return q;
+}
+
+__global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
+                        Acc128* acc) {
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
+  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
+  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 n13 = 0, n17 = 0;
+  while (true) {
+    int64_t it = next_item(qctr, g.n, &sh_item);
+    if (it < 0) break;
+    int64_t i = g.n - 1 - it;
+    int64_t b0 = g.R[i], e0 = g.R[i + 1];
+    if (e0 == b0) continue;
+    if (threadIdx.x == 0) *nt = 0;
+    __syncthreads();
+    for (int64_t p = b0 + wid; p < e0; p += nw) {
+      int32_t c = g.C[p];
+      int64_t cb = g.R[c], ce = g.rev[p];       // N(c) below i
+      for (int64_t q = cb + lane; q < ce; q += 32) {
+        int32_t j = g.C[q];
+        if (atomicAdd(&w[j], 1u) == 0) tl[atomicAdd(nt, 1u)] = j;
+      }
+    }
+    __syncthreads();
+    unsigned ntc = *nt;
+    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) n13 += ch3(w[tl[t]]);
+    // diamonds with tip i: triangle (i, x, y), x < y, j in U(x,y), j < i
+    for (int64_t p = b0 + wid; p < e0; p += nw) {
+      int32_t x = g.C[p];
+      if (T[p] == 0) continue;                  // no triangle on (i, x)
+      int64_t ub = tl3.off[p], ue = ub + T[p];
+      for (int64_t r = ub; r < ue; ++r) {       // y in U(i,x), ascending
+        int32_t y = tl3.U[r];
+        if (y <= x) continue;
+        int64_t pxy = find_slot(g, x, y);
+        int64_t vb = tl3.off[pxy], ve = vb + T[pxy];
+        for (int64_t s = vb + lane; s < ve; s += 32) {
+          int32_t j = tl3.U[s];
+          if (j >= i) break;
+          n17 += (u128)(w[j] - 2);
+        }
+      }
+    }
+    __syncthreads();
+    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
+    __syncthreads();
+  }
+  LocalAcc<2> la;
+  la.v[0] = n13;
+  la.v[1] = n17;
+  const int ids[2] = {ACC_N13, ACC_N17};
+  flush_acc(la, ids, acc, sh);
+}
+
+// ============================================================================
+// Thm 11: N18 (wheels) = sum over centres c of the 4-cycles of G[N(c)],
+// counted by the 4-cycle rule inside the neighbourhood: for u in N(c) and
+// v < u, C(w_c(u,v), 2) with w_c(u,v) = |{k in N(c) cap N(u) cap N(v): k < u}|.
+// Work items are (centre, one neighbour u); CTA-wide counters over v.
+// ============================================================================
+__global__ void k_wheels(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
+                         Acc128* acc) {
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
+  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
+  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 n18 = 0;
+  while (true) {
+    // item = a slot p = (c -> u); slots in order
+    int64_t p = next_item(qctr, g.nnz, &sh_item);
+    if (p < 0) break;
+    uint32_t tcu = T[p];
+    if (tcu < 2) continue;
+    int32_t u = g.C[p];
+    // c = row of p: binary search over R (uniform across the block)
+    int64_t lo = 0, hi = g.n;
+    while (hi - lo > 1) { int64_t mid = (lo + hi) >> 1; if (g.R[mid] <= p) lo = mid; else hi = mid; }
+    int64_t c = lo;
+    if (threadIdx.x == 0) *nt = 0;
+    __syncthreads();
+    int64_t ub = tl3.off[p];
+    // k in U(c,u) with k < u
+    for (int64_t r = ub + wid; r < ub + tcu; r += nw) {
+      int32_t k = tl3.U[r];
+      if (k >= u) break;
+      int64_t pck = find_slot(g, c, k);
+      int64_t vb = tl3.off[pck], ve = vb + T[pck];
+      for (int64_t s = vb + lane; s < ve; s += 32) {
+        int32_t v = tl3.U[s];
+        if (v >= u) break;
+        if (atomicAdd(&w[v], 1u) == 0) tl[atomicAdd(nt, 1u)] = v;
+      }
+    }
+    __syncthreads();
+    unsigned ntc = *nt;
+    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) {
+      int32_t v = tl[t];
+      n18 += ch2(w[v]);
+      w[v] = 0;
+    }
+    __syncthreads();
+  }
+  LocalAcc<1> la;
+  la.v[0] = n18;
+  const int ids[1] = {ACC_N18};
+  flush_acc(la, ids, acc, sh);
+}
+
+// ============================================================================
+// Thm 13: 5-cycles.  For every directed 3-path i <- a -> b -> j (a < i,
+// a < b < j, b != i, j != i) add w'(i,j) = |{c in N(i) cap N(j) : c < max(i,j)}|.
+// Grouped by the pair (i, b): sum_b P2(i,b) * sum_{j in N+(b)} w'(i,j) with
+// P2(i,b) = |{a in N-(i) : b in N+(a)}| (each out-wedge pair visited once).
+// The paths whose own a or b is counted by w' are the directed tailed
+// triangles, subtracted through ACC_N8Z (pass A).
+// ============================================================================
+__global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss, Acc128* acc) {
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  uint32_t* wp = ss.cnt + (int64_t)blockIdx.x * ss.n;
+  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
+  uint32_t* p2 = ss.cnt2 + (int64_t)blockIdx.x * ss.n;
+  int32_t* tl2 = ss.touched2 + (int64_t)blockIdx.x * ss.n;
+  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 m = 0;
+  while (true) {
+    int64_t it = next_item(qctr, g.n, &sh_item);
+    if (it < 0) break;
+    int64_t i = g.n - 1 - it;
+    int64_t b0 = g.R[i], o = g.op[i], e0 = g.R[i + 1];
+    if (o == b0) continue;                      // needs an in-neighbour a
+    if (threadIdx.x == 0) { nt[0] = 0; nt[1] = 0; }
+    __syncthreads();
+    // w'(i, .): c < i -> every j in N(c); c > i -> j in N+(c)
+    for (int64_t p = b0 + wid; p < e0; p += nw) {
+      int32_t c = g.C[p];
+      int64_t cb = (p < o) ? g.R[c] : g.op[c], ce = g.R[c + 1];
+      for (int64_t q = cb + lane; q < ce; q += 32) {
+        int32_t j = g.C[q];
+        if (j == i) continue;
+        if (atomicAdd(&wp[j], 1u) == 0) tl[atomicAdd(&nt[0], 1u)] = j;
+      }
+    }
+    // P2(i, .)
+    for (int64_t p = b0 + wid; p < o; p += nw) {
+      int32_t a = g.C[p];
+      for (int64_t q = g.op[a] + lane; q < g.R[a + 1]; q += 32) {
+        int32_t b = g.C[q];
+        if (b == i) continue;
+        if (atomicAdd(&p2[b], 1u) == 0) tl2[atomicAdd(&nt[1], 1u)] = b;
+      }
+    }
+    __syncthreads();
+    unsigned n1 = nt[0], n2 = nt[1];
+    for (unsigned t = wid; t < n2; t += nw) {
+      int32_t b = tl2[t];
+      unsigned long long s = 0;
+      for (int64_t q = g.op[b] + lane; q < g.R[b + 1]; q += 32) s += wp[g.C[q]];
+      s = warp_sum_u64(s);
+      if (lane == 0) m += (u128)s * p2[b];
+    }
+    __syncthreads();
+    for (unsigned t = threadIdx.x; t < n1; t += blockDim.x) wp[tl[t]] = 0;
+    for (unsigned t = threadIdx.x; t < n2; t += blockDim.x) p2[tl2[t]] = 0;
+    __syncthreads();
+  }
+  LocalAcc<1> la;
+  la.v[0] = m;
+  const int ids[1] = {ACC_N8M};
+  flush_acc(la, ids, acc, sh);
+}
+
+// ============================================================================
+// Per-edge common-neighbour lists (the per-edge triangle lists of Thm 7),
+// sorted ascending, stored once per undirected edge and addressed from both
+// slots.  Built per higher endpoint y: N(y) goes into a membership table, and
+// for every lower neighbour x the row N(x) is filtered through it.
+// ============================================================================
+__global__ void k_tri_lists(DevGraph g, unsigned long long* qctr, const int64_t* off, const uint32_t* T, int32_t* U,
+                            uint32_t* bitmap_all, int hash_cap, unsigned* status) {
+  extern __shared__ int32_t smem[];
+  __shared__ int64_t sh_item;
+  int32_t* hk = smem;
+  int32_t* hv = hk + hash_cap;
+  uint32_t* bm = bitmap_all + (int64_t)blockIdx.x * ((g.n + 31) >> 5);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  while (true) {
+    int64_t it = next_item(qctr, g.n, &sh_item);
+    if (it < 0) break;
+    int64_t y = g.n - 1 - it;
+    int64_t yb = g.R[y], yo = g.op[y], ye = g.R[y + 1];
+    if (yo == yb) continue;
+    int dy = (int)(ye - yb);
+    bool small = 2 * dy <= hash_cap;
+    int hsz = small ? pow2_at_least(2 * dy) : 0;
+    PosHash H{hk, hv, hsz - 1};
+    if (small) {
+      for (int i = threadIdx.x; i < hsz; i += blockDim.x) hk[i] = -1;
+      __syncthreads();
+      for (int i = threadIdx.x; i < dy; i += blockDim.x) H.insert(g.C[yb + i], i);
+    } else {
+      for (int64_t p = yb + threadIdx.x; p < ye; p += blockDim.x) {
+        int32_t v = g.C[p];
+        atomicOr(&bm[v >> 5], 1u << (v & 31));
+      }
+    }
+    __syncthreads();
+    for (int64_t p = yb + wid; p < yo; p += nw) {   // x in N-(y)
+      int32_t x = g.C[p];
+      int64_t cs = g.rev[p];                        // canonical slot (x -> y)
+      int64_t out = off[cs];
+      uint32_t expect = T[cs];
+      uint32_t written = 0;
+      for (int64_t base = g.R[x]; base < g.R[x + 1]; base += 32) {
+        int64_t q = base + lane;
+        bool hit = false;
+        int32_t z = -1;
+        if (q < g.R[x + 1]) {
+          z = g.C[q];
+          hit = small ? (H.find(z) >= 0) : ((bm[z >> 5] >> (z & 31)) & 1u);
+        }
+        unsigned hm = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          unsigned k = written + __popc(hm & ((1u << lane) - 1u));
+          if (k < expect) U[out + k] = z;
+        }
+        written += __popc(hm);
+      }
+      if (lane == 0 && written != expect) set_err(status, DEVERR_BOUNDS);
+    }
+    __syncthreads();
+    if (!small)
+      for (int64_t p = yb + threadIdx.x; p < ye; p += blockDim.x) {
+        int32_t v = g.C[p];
+        atomicAnd(&bm[v >> 5], ~(1u << (v & 31)));
+      }
+    __syncthreads();
+  }
+}
+
+// list offsets: off[p] for canonical slots = scan of T; reverse slots share it
+__global__ void k_canon_counts(DevGraph g, const uint32_t* T, int64_t* cnt) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps) {
+    for (int64_t p = g.R[v] + lane; p < g.op[v]; p += 32) cnt[p] = 0;
+    for (int64_t p = g.op[v] + lane; p < g.R[v + 1]; p += 32) cnt[p] = T[p];
+  }
+}
+__global__ void k_share_offsets(DevGraph g, int64_t* off) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < g.n; v += nwarps)
+    for (int64_t p = g.op[v] + lane; p < g.R[v + 1]; p += 32) off[g.rev[p]] = off[p];
+}
+
+// ============================================================================
+// Per-edge and per-vertex closed-form sums (Thms 4, 8, 9): one warp per row,
+// canonical slots only for unordered sums.
+// ============================================================================
+__global__ void k_edge_sums(DevGraph g, const uint32_t* T, const unsigned long long* C4e,
+                            const unsigned long long* K4e, const unsigned long long* tv,
+                            const unsigned long long* C4v, const unsigned long long* K4v, Acc128* acc) {
+  __shared__ u128 sh[32];
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  LocalAcc<16> la;
+  la.zero();
+  for (int64_t v = warp; v < g.n; v += nwarps) {
+    unsigned long long dv = (unsigned long long)dg_deg(g, v), tvv = tv[v];
+    for (int64_t p = g.R[v] + lane; p < g.R[v + 1]; p += 32) {
+      int32_t u = g.C[p];
+      unsigned long long du = (unsigned long long)dg_deg(g, u), te = T[p];
+      // ordered (v -> u)
+      la.v[0] += (u128)(tvv - te) * (du - 1);                       // N5 first term
+      if (te >= 2) la.v[1] += ch2(te) * (dv - 3);                   // N11
+      if (u > v) {                                                  // unordered
+        la.v[2] += ch2(te);                                         // D
+        la.v[3] += ch3(te);                                         // N14
+        if (te) la.v[4] += (u128)te * (dv - 2) * (du - 2);          // N6 first term
+        la.v[5] += (u128)C4e[p] * te;                               // N12 first term
+        if (K4e[p]) la.v[6] += (u128)K4e[p] * (te - 2);             // N19
+      }
+    }
+    if (lane == 0) {
+      if (dv >= 2) la.v[7] += (u128)tvv * (dv - 2);                 // TT
+      if (dv >= 2) la.v[8] += (u128)tvv * ch2(dv - 2);              // N4
+      la.v[9] += ch2(tvv);                                          // N9 first term
+      if (C4v[v]) la.v[10] += (u128)C4v[v] * (dv - 2);              // N7 first term
+      if (K4v[v]) la.v[11] += (u128)K4v[v] * (dv - 3);              // N15
+      la.v[12] += (u128)tvv * dv;                                   // P3+K2 / K3+K2 terms
+    }
+  }
+  const int ids[13] = {ACC_N5A, ACC_N11, ACC_D, ACC_N14, ACC_N6A, ACC_N12A, ACC_N19,
+                       ACC_TT, ACC_N4, ACC_N9A, ACC_N7A, ACC_N15, ACC_TD};
+  LocalAcc<13> l13;
+  for (int i = 0; i < 13; ++i) l13.v[i] = la.v[i];
+  flush_acc(l13, ids, acc, sh);
+}
+
+// ============================================================================
+// Assembly (Thm 3, App. A; Thms 4, 8-14; App. B).  One thread; all arithmetic
+// modulo 2^128, which is exact because every final count is below 2^127.
+// out: induced c3[4], c4[11], c5[34], then non-induced n3, n4, n5 (u128 each).
+// ============================================================================
+struct ConvTables {
+  long long a3[4 * 4];
+  long long a4[11 * 11];
+  long long a5[34 * 34];
+};
+
+__device__ __forceinline__ u128 cnk(u128 n, int k) {
+  // C(n, k) for k <= 5 with n < 2^64: exact in 128-bit (product of k terms / k!)
+  if (n < (u128)k) return 0;
+  u128 r = 1;
+  for (int i = 0; i < k; ++i) r = r * (n - i) / (i + 1);
+  return r;
+}
+
+__global__ void k_assemble(const Acc128* acc, unsigned long long n_, unsigned long long m_, ConvTables tabs,
+                           unsigned long long* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  u128 A[ACC_COUNT];
+  for (int i = 0; i < ACC_COUNT; ++i) A[i] = ((u128)acc[i].hi << 64) | acc[i].lo;
+  u128 n = n_, m = m_;
+  u128 W = A[ACC_W], T = A[ACC_T], TT = A[ACC_TT], C4 = A[ACC_C4], D = A[ACC_D];
+  u128 K4 = A[ACC_K4] / 3, S3 = A[ACC_S3];
+  u128 P4 = A[ACC_P4A] - 3 * T;
+  u128 N[35];
+  N[1] = A[ACC_S4];
+  N[2] = A[ACC_N2A] - 2 * TT;
+  N[3] = A[ACC_N3A] - 4 * C4 - 2 * TT - 3 * T;
+  N[4] = A[ACC_N4];
+  N[5] = A[ACC_N5A] - 4 * D;
+  N[6] = A[ACC_N6A] - 2 * D;
+  N[7] = A[ACC_N7A] - 2 * D;
+  N[8] = A[ACC_N8M] - A[ACC_N8Z];
+  N[9] = A[ACC_N9A] - 2 * D;
+  N[10] = A[ACC_N10A] - 12 * K4;
+  N[11] = A[ACC_N11];
+  N[12] = A[ACC_N12A] - 4 * D;
+  N[13] = A[ACC_N13];
+  N[14] = A[ACC_N14];
+  N[15] = A[ACC_N15];
+  N[16] = A[ACC_N16A] - 12 * K4;
+  N[17] = A[ACC_N17];
+  N[18] = A[ACC_N18];
+  N[19] = A[ACC_N19];
+  N[20] = A[ACC_N20];
+  N[21] = A[ACC_N21];
+  N[22] = cnk(n, 5);
+  N[23] = n >= 2 ? m * cnk(n - 2, 3) : 0;
+  N[24] = n >= 4 ? (cnk(m, 2) - W) * (n - 4) : 0;
+  N[25] = n >= 3 ? W * cnk(n - 3, 2) : 0;
+  N[26] = n >= 3 ? T * cnk(n - 3, 2) : 0;
+  N[27] = n >= 4 ? S3 * (n - 4) : 0;
+  N[28] = n >= 4 ? P4 * (n - 4) : 0;
+  N[29] = n >= 4 ? TT * (n - 4) : 0;
+  N[30] = n >= 4 ? C4 * (n - 4) : 0;
+  N[31] = n >= 4 ? D * (n - 4) : 0;
+  N[32] = n >= 4 ? K4 * (n - 4) : 0;
+  N[33] = W * m - A[ACC_D2D] - A[ACC_DNBR] + 2 * W + 3 * T;
+  N[34] = T * m - A[ACC_TD] + 3 * T;
+  u128 n4[11] = {S3, P4, TT, C4, D, K4, cnk(n, 4), n >= 2 ? m * cnk(n - 2, 2) : 0, cnk(m, 2) - W,
+                 n >= 3 ? W * (n - 3) : 0, n >= 3 ? T * (n - 3) : 0};
+  u128 n3[4] = {cnk(n, 3), n >= 2 ? m * (n - 2) : 0, W, T};
+  // induced = A^-1 * non-induced (signed integer matrix, arithmetic mod 2^128)
+  u128* o = (u128*)out;
+  for (int i = 0; i < 4; ++i) {
+    u128 s = 0;
+    for (int j = 0; j < 4; ++j) s += (u128)(__int128)tabs.a3[i * 4 + j] * n3[j];
+    o[i] = s;
+    o[49 + i] = n3[i];
+  }
+  for (int i = 0; i < 11; ++i) {
+    u128 s = 0;
+    for (int j = 0; j < 11; ++j) s += (u128)(__int128)tabs.a4[i * 11 + j] * n4[j];
+    o[4 + i] = s;
+    o[49 + 4 + i] = n4[i];
+  }
+  for (int i = 0; i < 34; ++i) {
+    u128 s = 0;
+    for (int j = 0; j < 34; ++j) s += (u128)(__int128)tabs.a5[i * 34 + j] * N[j + 1];
+    o[15 + i] = s;
+    o[49 + 15 + i] = N[i + 1];
+  }
+}
+
+// ============================================================================
+// Host orchestration.
+// ============================================================================
+static unsigned grid_for(int64_t work, int threads, int sms) {
+  int64_t b = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sms * 8;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// item lists of pass A/B: vertices by out-degree class
+__global__ void k_split_items(DevGraph g, int32_t* small, int32_t* large, unsigned long long* cnts, int small_max) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < g.n; k += stride) {
+    int64_t x = g.n - 1 - k;
+    int64_t d = g.R[x + 1] - g.op[x];
+    if (d < 2) continue;
+    if (d <= small_max) small[atomicAdd(&cnts[0], 1ull)] = (int32_t)x;
+    else large[atomicAdd(&cnts[1], 1ull)] = (int32_t)x;
+  }
+}
+
+// max over vertices of d+ x ceil(d- / 64) (words of the D bit sets) and max d+
+__global__ void k_clique_dims(DevGraph g, unsigned long long* out) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long mw = 0, md = 0;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < g.n; x += stride) {
+    unsigned long long dp = (unsigned long long)(g.R[x + 1] - g.op[x]);
+    unsigned long long dm = (unsigned long long)(g.op[x] - g.R[x]);
+    if (dp >= 2) {
+      unsigned long long wds = dp * ((dm + 63) / 64);
+      if (wds > mw) mw = wds;
+    }
+    if (dp > md) md = dp;
+  }
+  atomicMax(&out[0], mw);
+  atomicMax(&out[1], md);
+}
+
+size_t census_scratch_bytes(int64_t n, int64_t nnz, int sms, int cta_per_sm) {
+  (void)sms; (void)cta_per_sm;
+  return 0;   // scratch is allocated inside run_census (sizes depend on the graph)
+}
+
+static cudaError_t check_status(unsigned* d_status, cudaStream_t s, unsigned* h) {
+  cudaError_t e = cudaMemcpyAsync(h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+  cudaError_t alloc(size_t b) { return cudaMalloc(&p, b > 0 ? b : 16); }
+  template <class T> T* as() { return (T*)p; }
+};
+
+#define ESC_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return _e; } while (0)
+
+cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, void* /*scratch*/,
+                       size_t /*scratch_bytes*/, const CensusConfig& cfg, unsigned long long* d_out,
+                       unsigned* d_status, PerElement* pe_out, Oriented* or_out, cudaStream_t s) {
+  const int sms = cfg.sms > 0 ? cfg.sms : 1;
+  int ev = 0;
+  auto phase = [&]() {
+    if (cfg.phase_events && ev < cfg.num_phase_events) cudaEventRecord(cfg.phase_events[ev++], s);
+  };
+  phase();
+  // ---------------- orientation (Sec. 3.2)
+  DevBuf arena_buf;
+  DeviceArena arena;
+  int64_t nk = (n > nnz ? n : nnz) + 16;
+  size_t arena_bytes = (size_t)nk * 8 * 2 + (size_t)(n + 16) * 8 + (size_t)(nk / 4096 + 2) * 256 * 8 * 2 + (1 << 22);
+  ESC_TRY(arena_buf.alloc(arena_bytes));
+  arena.base = arena_buf.as<char>();
+  arena.cap = arena_bytes;
+
+  DevBuf b_perm, b_rank, b_R, b_C, b_op, b_rev;
+  ESC_TRY(b_perm.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_rank.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_R.alloc(sizeof(int64_t) * (n + 1)));
+  ESC_TRY(b_C.alloc(sizeof(int32_t) * (nnz + 1)));
+  ESC_TRY(b_op.alloc(sizeof(int64_t) * (n + 1)));
+  ESC_TRY(b_rev.alloc(sizeof(int64_t) * (nnz + 1)));
+  Oriented o;
+  o.perm = b_perm.as<int32_t>();
+  o.rank = b_rank.as<int32_t>();
+  o.R = b_R.as<int64_t>();
+  o.C = b_C.as<int32_t>();
+  o.op = b_op.as<int64_t>();
+  o.rev = b_rev.as<int64_t>();
+  ESC_TRY(orient(rp, col, n, nnz, o, arena, s, sms));
+  phase();
+
+  DevGraph g{n, nnz, o.R, o.C, o.op, o.rev};
+  // ---------------- per-element arrays and accumulators
+  DevBuf b_T, b_K4e, b_C4e, b_tv, b_C4v, b_K4v, b_acc, b_ctr;
+  ESC_TRY(b_T.alloc(sizeof(uint32_t) * (nnz + 1)));
+  ESC_TRY(b_K4e.alloc(sizeof(unsigned long long) * (nnz + 1)));
+  ESC_TRY(b_C4e.alloc(sizeof(unsigned long long) * (nnz + 1)));
+  ESC_TRY(b_tv.alloc(sizeof(unsigned long long) * (n + 1)));
+  ESC_TRY(b_C4v.alloc(sizeof(unsigned long long) * (n + 1)));
+  ESC_TRY(b_K4v.alloc(sizeof(unsigned long long) * (n + 1)));
+  ESC_TRY(b_acc.alloc(sizeof(Acc128) * ACC_COUNT));
+  ESC_TRY(b_ctr.alloc(sizeof(unsigned long long) * 16));
+  uint32_t* T = b_T.as<uint32_t>();
+  unsigned long long *K4e = b_K4e.as<unsigned long long>(), *C4e = b_C4e.as<unsigned long long>();
+  unsigned long long *tv = b_tv.as<unsigned long long>(), *C4v = b_C4v.as<unsigned long long>(),
+                     *K4v = b_K4v.as<unsigned long long>();
+  Acc128* acc = b_acc.as<Acc128>();
+  unsigned long long* ctr = b_ctr.as<unsigned long long>();
+  cudaMemsetAsync(T, 0, sizeof(uint32_t) * (nnz + 1), s);
+  cudaMemsetAsync(K4e, 0, sizeof(unsigned long long) * (nnz + 1), s);
+  cudaMemsetAsync(C4e, 0, sizeof(unsigned long long) * (nnz + 1), s);
+  cudaMemsetAsync(C4v, 0, sizeof(unsigned long long) * (n + 1), s);
+  cudaMemsetAsync(acc, 0, sizeof(Acc128) * ACC_COUNT, s);
+  cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
+
+  const int TPB = 256;
+  if (n > 0) k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, acc);
+
+  // ---------------- item lists for the out-neighbourhood passes
+  DevBuf b_small, b_large, b_dims;
+  ESC_TRY(b_small.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_large.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_dims.alloc(sizeof(unsigned long long) * 2));
+  cudaMemsetAsync(b_dims.p, 0, sizeof(unsigned long long) * 2, s);
+  if (n > 0) {
+    k_split_items<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), b_large.as<int32_t>(), ctr, SMALL_DPLUS);
+    k_clique_dims<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_dims.as<unsigned long long>());
+  }
+  unsigned long long hcnt[16] = {0}, dims[2] = {0, 0};
+  cudaMemcpyAsync(hcnt, ctr, sizeof(hcnt), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(dims, b_dims.p, sizeof(dims), cudaMemcpyDeviceToHost, s);
+  ESC_TRY(cudaStreamSynchronize(s));
+  int64_t nsmall = (int64_t)hcnt[0], nlarge = (int64_t)hcnt[1];
+  int dmax = (int)dims[1];
+  if (dmax < SMALL_DPLUS + 1) dmax = SMALL_DPLUS + 1;
+  cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
+
+  // ---------------- pass A: triangles
+  int hcap_a = pow2_at_least(2 * dmax);
+  size_t smem_a = sizeof(int32_t) * (2 * (size_t)hcap_a) + sizeof(uint32_t) * dmax;
+  int grid_sweep = sms * (cfg.cta_per_sm > 0 ? cfg.cta_per_sm : 1);
+  if (nsmall > 0)
+    k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, acc);
+  if (nlarge > 0) {
+    if (smem_a > 48 * 1024) ESC_TRY(cudaFuncSetAttribute(k_tri_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+    k_tri_large<<<(unsigned)std::min<int64_t>(grid_sweep, nlarge), 512, smem_a, s>>>(
+        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, acc, hcap_a);
+  }
+  if (n > 0) {
+    k_sym_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv);
+    k_vertex_from_edges_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv);
+  }
+  phase();
+
+  // ---------------- pass B: cliques and per-triangle sums
+  {
+    // all vertices with d+ >= 2 go through the CTA path (the bit matrix needs it)
+    int64_t nitems = nsmall + nlarge;
+    DevBuf b_items;
+    ESC_TRY(b_items.alloc(sizeof(int32_t) * (nitems + 1)));
+    if (nlarge) cudaMemcpyAsync(b_items.p, b_large.p, sizeof(int32_t) * nlarge, cudaMemcpyDeviceToDevice, s);
+    if (nsmall) cudaMemcpyAsync(b_items.as<int32_t>() + nlarge, b_small.p, sizeof(int32_t) * nsmall, cudaMemcpyDeviceToDevice, s);
+    int W_cap = (dmax + 63) >> 6;
+    int hcap = pow2_at_least(2 * dmax);
+    size_t smem_b = sizeof(uint64_t) * ((size_t)dmax * W_cap + dmax) + sizeof(int32_t) * (2 * (size_t)hcap) +
+                    sizeof(uint32_t) * dmax;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem_b + 1024 > (size_t)smem_optin) {
+      return cudaErrorInvalidConfiguration;   // out-degree beyond the shared-memory bit matrix
+    }
+    ESC_TRY(cudaFuncSetAttribute(k_clique_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    int blocks_b = sms;   // one CTA per SM (large shared memory)
+    unsigned long long dwords = dims[0] > 0 ? dims[0] : 1;
+    DevBuf b_D;
+    ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
+    CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
+    if (nitems > 0)
+      k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems), 512, smem_b, s>>>(
+          g, b_items.as<int32_t>(), nitems, ctr + 1, T, K4e, acc, cs, hcap, dmax, d_status);
+    if (n > 0) {
+      k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e);
+      k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e, K4v, 3);
+    }
+    ESC_TRY(cudaStreamSynchronize(s));   // b_items / b_D go out of scope
+  }
+  phase();
+
+  // ---------------- sweep scratch
+  DevBuf b_cnt, b_tl, b_cnt2, b_tl2, b_nt;
+  ESC_TRY(b_cnt.alloc(sizeof(uint32_t) * (size_t)n * grid_sweep + 16));
+  ESC_TRY(b_tl.alloc(sizeof(int32_t) * (size_t)n * grid_sweep + 16));
+  ESC_TRY(b_cnt2.alloc(sizeof(uint32_t) * (size_t)n * grid_sweep + 16));
+  ESC_TRY(b_tl2.alloc(sizeof(int32_t) * (size_t)n * grid_sweep + 16));
+  ESC_TRY(b_nt.alloc(sizeof(unsigned) * 2 * grid_sweep));
+  cudaMemsetAsync(b_cnt.p, 0, sizeof(uint32_t) * (size_t)n * grid_sweep + 16, s);
+  cudaMemsetAsync(b_cnt2.p, 0, sizeof(uint32_t) * (size_t)n * grid_sweep + 16, s);
+  SweepScratch ss{b_cnt.as<uint32_t>(), b_tl.as<int32_t>(), b_cnt2.as<uint32_t>(), b_tl2.as<int32_t>(),
+                  b_nt.as<unsigned>(), n};
+
+  // ---------------- 4-cycles (Thm 5)
+  if (n > 0) {
+    k_cycles4<<<grid_sweep, 512, 0, s>>>(g, ctr + 2, ss, C4e, C4v, acc);
+    k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, C4e);
+  }
+  phase();
+
+  // ---------------- closed forms over vertices and edges
+  if (n > 0)
+    k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, acc);
+
+  // ---------------- common-neighbour lists
+  DevBuf b_off, b_U, b_bm;
+  ESC_TRY(b_off.alloc(sizeof(int64_t) * (nnz + 2)));
+  int64_t* off = b_off.as<int64_t>();
+  if (n > 0) k_canon_counts<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, off);
+  ESC_TRY(exclusive_scan_i64(off, off, nnz, true, arena, s));
+  int64_t ulen = 0;
+  cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  ESC_TRY(cudaStreamSynchronize(s));
+  if (n > 0) k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off);
+  ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
+  int64_t bm_words = (n + 31) >> 5;
+  ESC_TRY(b_bm.alloc(sizeof(uint32_t) * (size_t)bm_words * grid_sweep + 16));
+  cudaMemsetAsync(b_bm.p, 0, sizeof(uint32_t) * (size_t)bm_words * grid_sweep + 16, s);
+  {
+    int hcap_l = 8192;
+    size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
+    ESC_TRY(cudaFuncSetAttribute(k_tri_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
+    if (n > 0)
+      k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, T, b_U.as<int32_t>(), b_bm.as<uint32_t>(),
+                                                  hcap_l, d_status);
+  }
+  TriLists tl3{off, b_U.as<int32_t>()};
+  phase();
+
+  // ---------------- pairs: N13, N17 (Thms 11, 12)
+  if (n > 0) k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, acc);
+  phase();
+  // ---------------- wheels: N18 (Thm 11)
+  if (nnz > 0) k_wheels<<<grid_sweep, 512, 0, s>>>(g, ctr + 5, ss, tl3, T, acc);
+  phase();
+  // ---------------- 5-cycles (Thm 13)
+  if (n > 0) k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, acc);
+  phase();
+
+  // ---------------- assembly
+  ConvTables tabs;
+  conversion_inverse(3, tabs.a3);
+  conversion_inverse(4, tabs.a4);
+  conversion_inverse(5, tabs.a5);
+  k_assemble<<<1, 32, 0, s>>>(acc, (unsigned long long)n, (unsigned long long)(nnz / 2), tabs, d_out);
+  phase();
+
+  if (pe_out) {
+    // hand the per-element arrays over to the caller (ownership moves)
+    pe_out->Te = T; b_T.p = nullptr;
+    pe_out->C4e = C4e; b_C4e.p = nullptr;
+    pe_out->K4e = K4e; b_K4e.p = nullptr;
+    pe_out->tv = tv; b_tv.p = nullptr;
+    pe_out->C4v = C4v; b_C4v.p = nullptr;
+    pe_out->K4v = K4v; b_K4v.p = nullptr;
+  }
+  if (or_out) {
+    *or_out = o;
+    b_perm.p = b_rank.p = b_R.p = b_C.p = b_op.p = b_rev.p = nullptr;
+  }
+  ESC_TRY(cudaStreamSynchronize(s));   // scratch buffers are freed on return
+  return cudaGetLastError();
+}
+
+}  // namespace esc

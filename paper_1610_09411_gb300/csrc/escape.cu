@@ -1,0 +1,490 @@
+// escape.cu -- the C ABI (include/escape.h): graph handles, the census entry
+// points, per-element output and the induced/non-induced conversion tables.
+#include "../../include/escape.h"
+#include "common.cuh"
+#include "internal.h"
+
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+struct escape_graph {
+  int64_t n = 0, nnz = 0;
+  int64_t* d_rp = nullptr;     // input CSR, original ids
+  int32_t* d_col = nullptr;
+  int device = 0, sms = 1;
+  int keep_pe = 0, cta_per_sm = 2;
+  bool has_pe = false;
+  esc::PerElement pe;
+  esc::Oriented ori;
+  float phase_ms[9] = {0};
+  int num_phases = 0;
+};
+
+namespace {
+
+escape_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return ESCAPE_OK;
+  if (e == cudaErrorMemoryAllocation) return ESCAPE_ENOMEM;
+  if (e == cudaErrorInvalidConfiguration) return ESCAPE_EOVERFLOW;
+  cudaGetLastError();   // clear a non-sticky error
+  return ESCAPE_ECUDA;
+}
+
+void free_pe(escape_graph* g) {
+  cudaFree(g->pe.Te); cudaFree(g->pe.C4e); cudaFree(g->pe.K4e);
+  cudaFree(g->pe.tv); cudaFree(g->pe.C4v); cudaFree(g->pe.K4v);
+  g->pe = esc::PerElement{};
+  cudaFree(g->ori.perm); cudaFree(g->ori.rank); cudaFree(g->ori.R); cudaFree(g->ori.C);
+  cudaFree(g->ori.op); cudaFree(g->ori.rev);
+  g->ori = esc::Oriented{};
+  g->has_pe = false;
+}
+
+// --------------------------------------------------------------------------
+// Pattern catalogue for the conversion tables (App. B), 0-based vertex pairs:
+// 5-vertex patterns 1-21 of the paper's connected-pattern figure, 22-32 of its
+// disconnected-pattern figure, then wedge + edge and triangle + edge.
+// --------------------------------------------------------------------------
+struct Pat { int ne; unsigned char e[10][2]; };
+
+const Pat kPat5[34] = {
+  {4, {{0,1},{0,2},{0,3},{0,4}}},
+  {4, {{0,1},{0,2},{0,3},{1,4}}},
+  {4, {{0,1},{0,2},{1,3},{2,4}}},
+  {5, {{0,1},{0,2},{1,2},{2,3},{2,4}}},
+  {5, {{0,1},{0,2},{1,2},{1,3},{3,4}}},
+  {5, {{0,1},{0,2},{1,2},{1,3},{2,4}}},
+  {5, {{0,1},{0,2},{1,3},{2,3},{2,4}}},
+  {5, {{0,1},{0,2},{1,3},{2,4},{3,4}}},
+  {6, {{0,1},{0,2},{1,2},{2,3},{2,4},{3,4}}},
+  {6, {{0,1},{0,2},{0,3},{1,3},{2,3},{2,4}}},
+  {6, {{0,1},{0,2},{1,2},{1,3},{2,3},{2,4}}},
+  {6, {{0,1},{0,2},{1,3},{2,3},{2,4},{3,4}}},
+  {6, {{0,1},{0,2},{0,3},{1,4},{2,4},{3,4}}},
+  {7, {{0,1},{0,2},{0,3},{0,4},{1,4},{2,4},{3,4}}},
+  {7, {{0,1},{0,2},{0,3},{1,2},{1,3},{2,3},{2,4}}},
+  {7, {{0,1},{0,2},{1,2},{1,3},{2,3},{2,4},{3,4}}},
+  {7, {{0,1},{0,2},{0,3},{1,2},{1,3},{2,4},{3,4}}},
+  {8, {{0,1},{0,2},{0,3},{0,4},{1,2},{1,3},{2,4},{3,4}}},
+  {8, {{0,1},{0,2},{0,3},{1,2},{1,3},{2,3},{2,4},{3,4}}},
+  {9, {{0,2},{0,3},{0,4},{1,2},{1,3},{1,4},{2,3},{2,4},{3,4}}},
+  {10, {{0,1},{0,2},{0,3},{0,4},{1,2},{1,3},{1,4},{2,3},{2,4},{3,4}}},
+  {0, {}},
+  {1, {{0,1}}},
+  {2, {{0,1},{2,3}}},
+  {2, {{0,1},{1,2}}},
+  {3, {{0,1},{0,2},{1,2}}},
+  {3, {{0,1},{0,2},{0,3}}},
+  {3, {{0,1},{0,2},{1,3}}},
+  {4, {{0,1},{0,2},{0,3},{1,2}}},
+  {4, {{0,1},{0,2},{1,3},{2,3}}},
+  {5, {{0,1},{0,2},{0,3},{1,2},{1,3}}},
+  {6, {{0,1},{0,2},{0,3},{1,2},{1,3},{2,3}}},
+  {3, {{0,1},{1,2},{3,4}}},
+  {4, {{0,1},{0,2},{1,2},{3,4}}},
+};
+const Pat kPat4[11] = {
+  {3, {{0,1},{0,2},{0,3}}},
+  {3, {{0,1},{0,2},{1,3}}},
+  {4, {{0,1},{0,2},{0,3},{1,2}}},
+  {4, {{0,1},{0,2},{1,3},{2,3}}},
+  {5, {{0,1},{0,2},{0,3},{1,2},{1,3}}},
+  {6, {{0,1},{0,2},{0,3},{1,2},{1,3},{2,3}}},
+  {0, {}},
+  {1, {{0,1}}},
+  {2, {{0,1},{2,3}}},
+  {2, {{0,1},{1,2}}},
+  {3, {{0,1},{0,2},{1,2}}},
+};
+const Pat kPat3[4] = {
+  {0, {}}, {1, {{0,1}}}, {2, {{0,1},{0,2}}}, {3, {{0,1},{0,2},{1,2}}},
+};
+
+// adjacency matrix of a pattern as a k x k bool table
+void pat_adj(const Pat& p, int k, bool adj[5][5]) {
+  for (int a = 0; a < 5; ++a) for (int b = 0; b < 5; ++b) adj[a][b] = false;
+  for (int t = 0; t < p.ne; ++t) { adj[p.e[t][0]][p.e[t][1]] = true; adj[p.e[t][1]][p.e[t][0]] = true; }
+  (void)k;
+}
+
+// number of bijections sigma of {0..k-1} with sigma(E_small) subset of E_big
+long long embeddings(const Pat& small, const Pat& big, int k) {
+  bool As[5][5], Ab[5][5];
+  pat_adj(small, k, As);
+  pat_adj(big, k, Ab);
+  int perm[5] = {0, 1, 2, 3, 4};
+  long long cnt = 0;
+  // lexicographic permutations
+  while (true) {
+    bool ok = true;
+    for (int a = 0; a < k && ok; ++a)
+      for (int b = a + 1; b < k && ok; ++b)
+        if (As[a][b] && !Ab[perm[a]][perm[b]]) ok = false;
+    if (ok) ++cnt;
+    int i = k - 2;
+    while (i >= 0 && perm[i] > perm[i + 1]) --i;
+    if (i < 0) break;
+    int j = k - 1;
+    while (perm[j] < perm[i]) --j;
+    int t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    for (int l = i + 1, r = k - 1; l < r; ++l, --r) { t = perm[l]; perm[l] = perm[r]; perm[r] = t; }
+  }
+  return cnt;
+}
+
+}  // namespace
+
+namespace esc {
+// A[i][j] = (embeddings of pattern i into pattern j) / |Aut(pattern i)| = the
+// number of spanning subgraphs of pattern j isomorphic to pattern i; its
+// inverse by back-substitution (A is unit triangular when classes are ordered
+// by edge count).
+void conversion_inverse(int k, long long* Ainv) {
+  const Pat* P = k == 3 ? kPat3 : (k == 4 ? kPat4 : kPat5);
+  int c = k == 3 ? 4 : (k == 4 ? 11 : 34);
+  std::vector<long long> A((size_t)c * c);
+  for (int i = 0; i < c; ++i) {
+    long long aut = embeddings(P[i], P[i], k);
+    for (int j = 0; j < c; ++j) A[(size_t)i * c + j] = embeddings(P[i], P[j], k) / aut;
+  }
+  // X = A^-1: column by column, rows from most edges to fewest
+  std::vector<int> order(c);
+  for (int i = 0; i < c; ++i) order[i] = i;
+  for (int a = 0; a < c; ++a)
+    for (int b = a + 1; b < c; ++b)
+      if (P[order[b]].ne > P[order[a]].ne) { int t = order[a]; order[a] = order[b]; order[b] = t; }
+  for (int col = 0; col < c; ++col) {
+    std::vector<long long> x(c, 0);
+    for (int oi = 0; oi < c; ++oi) {
+      int i = order[oi];
+      long long s = (i == col) ? 1 : 0;
+      for (int j = 0; j < c; ++j)
+        if (j != i && A[(size_t)i * c + j]) s -= A[(size_t)i * c + j] * x[j];
+      x[i] = s;    // A[i][i] == 1
+    }
+    for (int i = 0; i < c; ++i) Ainv[(size_t)i * c + col] = x[i];
+  }
+}
+}  // namespace esc
+
+namespace {
+
+int device_sms(int dev) {
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+__global__ void k_rebase_rows(const int64_t* rp, int64_t n, int64_t base, int64_t* out) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) out[i] = rp[i] - base;
+}
+
+// input slot p (u -> v, original ids) -> value at the rank-space slot
+__global__ void k_map_edges(const int64_t* rp, const int32_t* col, int64_t n, const int32_t* rank,
+                            const int64_t* R, const int32_t* C, const uint32_t* Te, const unsigned long long* C4e,
+                            const unsigned long long* K4e, unsigned long long* oT, unsigned long long* oC4,
+                            unsigned long long* oK4) {
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int lane = threadIdx.x & 31;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    int32_t ru = rank[u];
+    for (int64_t p = rp[u] + lane; p < rp[u + 1]; p += 32) {
+      int32_t rv = rank[col[p]];
+      int64_t q = lower_bound_i32(C, R[ru], R[ru + 1], rv);
+      oT[p] = Te[q];
+      oC4[p] = C4e[q];
+      oK4[p] = K4e[q];
+    }
+  }
+}
+
+__global__ void k_map_vertices(int64_t n, const int32_t* rank, const unsigned long long* tv,
+                               const unsigned long long* C4v, const unsigned long long* K4v, unsigned long long* ot,
+                               unsigned long long* oc, unsigned long long* ok) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+    int32_t r = rank[u];
+    ot[u] = tv[r];
+    oc[u] = C4v[r];
+    ok[u] = K4v[r];
+  }
+}
+
+escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_col, int64_t n, int64_t nnz,
+                         escape_census* out, cudaStream_t s, bool keep, esc::PerElement* pe, esc::Oriented* ori,
+                         float* phase_ms, int* nphase) {
+  unsigned long long* d_out = nullptr;
+  unsigned* d_status = nullptr;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(escape_census));
+  if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
+  if (e != cudaSuccess) { cudaFree(d_out); return from_cuda(e); }
+  cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
+  cudaEvent_t evs[10];
+  int nev = phase_ms ? 10 : 0;
+  for (int i = 0; i < nev; ++i) cudaEventCreate(&evs[i]);
+  esc::CensusConfig cfg;
+  cfg.sms = g->sms;
+  cfg.cta_per_sm = g->cta_per_sm;
+  cfg.keep_per_element = keep;
+  cfg.phase_events = nev ? evs : nullptr;
+  cfg.num_phase_events = nev;
+  e = esc::run_census(d_rp, d_col, n, nnz, nullptr, 0, cfg, d_out, d_status, keep ? pe : nullptr,
+                      keep ? ori : nullptr, s);
+  escape_status st = from_cuda(e);
+  unsigned hstat = 0;
+  if (st == ESCAPE_OK) {
+    escape_census tmp;
+    e = cudaMemcpyAsync(&tmp, d_out, sizeof(escape_census), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = from_cuda(e);
+    if (st == ESCAPE_OK && hstat != 0) st = ESCAPE_EINTERNAL;
+    if (st == ESCAPE_OK) *out = tmp;
+  }
+  if (nev) {
+    int phases = 0;
+    for (int i = 0; i + 1 < nev; ++i) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, evs[i], evs[i + 1]) == cudaSuccess) { phase_ms[i] = ms; phases = i + 1; }
+    }
+    cudaGetLastError();
+    *nphase = phases;
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(evs[i]);
+  }
+  cudaFree(d_out);
+  cudaFree(d_status);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* escape_status_str(escape_status s) {
+  switch (s) {
+    case ESCAPE_OK: return "ok";
+    case ESCAPE_EINVAL: return "invalid argument or malformed graph";
+    case ESCAPE_ENOMEM: return "out of memory";
+    case ESCAPE_ECUDA: return "CUDA error";
+    case ESCAPE_EOVERFLOW: return "size beyond supported limits";
+    case ESCAPE_ETIMEOUT: return "device wait timed out";
+    case ESCAPE_EINTERNAL: return "device consistency check failed";
+  }
+  return "unknown status";
+}
+
+escape_status escape_load_csr(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col, uint32_t flags,
+                              void* stream, escape_graph** out) {
+  if (!out || n < 0 || n > 2147483647LL || nnz < 0 || (n > 0 && !row_ptr) || (nnz > 0 && !col))
+    return ESCAPE_EINVAL;
+  if (nnz > ((int64_t)1 << 40)) return ESCAPE_EOVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool dev_ptrs = (flags & ESCAPE_DEVICE_PTRS) != 0;
+  escape_graph* g = new (std::nothrow) escape_graph;
+  if (!g) return ESCAPE_ENOMEM;
+  cudaGetDevice(&g->device);
+  g->sms = device_sms(g->device);
+  // host-side checks of the row pointer (host input) before any copy
+  if (!dev_ptrs && n > 0) {
+    if (row_ptr[0] != 0 || row_ptr[n] != nnz) { delete g; return ESCAPE_EINVAL; }
+    for (int64_t i = 0; i < n; ++i)
+      if (row_ptr[i + 1] < row_ptr[i]) { delete g; return ESCAPE_EINVAL; }
+  }
+  int64_t* d_rp = nullptr;
+  int32_t* d_col = nullptr;
+  unsigned* d_status = nullptr;
+  cudaError_t e = cudaMalloc(&d_rp, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_col, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
+  if (e != cudaSuccess) { cudaFree(d_rp); cudaFree(d_col); delete g; return from_cuda(e); }
+  cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n > 0) e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n + 1), kind, s);
+  else e = cudaMemsetAsync(d_rp, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, kind, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
+  escape_status st = from_cuda(e);
+  if (st == ESCAPE_OK && dev_ptrs && n > 0) {
+    int64_t ends[2];
+    e = cudaMemcpyAsync(&ends[0], d_rp, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], d_rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = from_cuda(e);
+    if (st == ESCAPE_OK && (ends[0] != 0 || ends[1] != nnz)) st = ESCAPE_EINVAL;
+  }
+  if (st == ESCAPE_OK && (flags & ESCAPE_NORMALIZE)) {
+    esc::DeviceArena arena;
+    size_t ab = (size_t)(2 * nnz + 16) * 8 * 3 + (size_t)((2 * nnz) / 4096 + 2) * 256 * 8 * 2 + (1 << 22);
+    e = cudaMalloc(&arena.base, ab);
+    if (e == cudaSuccess) {
+      arena.cap = ab;
+      int64_t *nrp = nullptr;
+      int32_t* ncol = nullptr;
+      int64_t nnz2 = 0;
+      e = esc::normalize_csr(n, nnz, d_rp, d_col, &nrp, &ncol, &nnz2, d_status, arena, s, g->sms);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(arena.base);
+      if (e == cudaSuccess) {
+        cudaFree(d_rp);
+        cudaFree(d_col);
+        d_rp = nrp;
+        d_col = ncol;
+        nnz = nnz2;
+      }
+    }
+    st = from_cuda(e);
+  } else if (st == ESCAPE_OK) {
+    e = esc::validate_csr(n, d_rp, d_col, d_status, s, g->sms);
+    st = from_cuda(e);
+  }
+  if (st == ESCAPE_OK) {
+    unsigned h = 0;
+    e = cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = from_cuda(e);
+    if (st == ESCAPE_OK && h) st = ESCAPE_EINVAL;
+  }
+  cudaFree(d_status);
+  if (st != ESCAPE_OK) { cudaFree(d_rp); cudaFree(d_col); delete g; return st; }
+  g->n = n;
+  g->nnz = nnz;
+  g->d_rp = d_rp;
+  g->d_col = d_col;
+  *out = g;
+  return ESCAPE_OK;
+}
+
+escape_status escape_graph_info(const escape_graph* g, int64_t* n, int64_t* m) {
+  if (!g) return ESCAPE_EINVAL;
+  if (n) *n = g->n;
+  if (m) *m = g->nnz / 2;
+  return ESCAPE_OK;
+}
+
+escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_per_sm) {
+  if (!g || cta_per_sm < 0 || cta_per_sm > 8) return ESCAPE_EINVAL;
+  g->keep_pe = keep_per_element ? 1 : 0;
+  g->cta_per_sm = cta_per_sm ? cta_per_sm : 2;
+  return ESCAPE_OK;
+}
+
+escape_status escape_census5(escape_graph* g, escape_census* out, void* stream) {
+  if (!g || !out) return ESCAPE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  free_pe(g);
+  escape_status st = census_one(g, g->d_rp, g->d_col, g->n, g->nnz, out, s, g->keep_pe != 0, &g->pe, &g->ori,
+                                g->phase_ms, &g->num_phases);
+  if (st == ESCAPE_OK && g->keep_pe) g->has_pe = true;
+  else free_pe(g);
+  return st;
+}
+
+escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offsets, const int64_t* row_ptr,
+                                   const int32_t* col, uint32_t flags, escape_census* out, void* stream) {
+  if (num_graphs < 0 || (num_graphs > 0 && (!vtx_offsets || !row_ptr || !out))) return ESCAPE_EINVAL;
+  if (num_graphs == 0) return ESCAPE_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool dev_ptrs = (flags & ESCAPE_DEVICE_PTRS) != 0;
+  std::vector<int64_t> voff(num_graphs + 1);
+  cudaError_t e;
+  if (dev_ptrs) {
+    e = cudaMemcpyAsync(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+  } else {
+    memcpy(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1));
+  }
+  if (voff[0] != 0) return ESCAPE_EINVAL;
+  for (int k = 0; k < num_graphs; ++k)
+    if (voff[k + 1] < voff[k] || voff[k + 1] - voff[k] > 2147483647LL) return ESCAPE_EINVAL;
+  int64_t rows = voff[num_graphs];
+  std::vector<int64_t> hrp;
+  const int64_t* rp_host = nullptr;
+  if (dev_ptrs) {
+    hrp.resize(rows + 1);
+    e = cudaMemcpyAsync(hrp.data(), row_ptr, sizeof(int64_t) * (rows + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    rp_host = hrp.data();
+  } else {
+    rp_host = row_ptr;
+  }
+  if (rp_host[0] != 0) return ESCAPE_EINVAL;
+  std::vector<escape_census> res(num_graphs);
+  std::vector<int64_t> local;
+  for (int k = 0; k < num_graphs; ++k) {
+    int64_t v0 = voff[k], n = voff[k + 1] - v0;
+    int64_t e0 = rp_host[v0], nnz = rp_host[v0 + n] - e0;
+    if (nnz < 0) return ESCAPE_EINVAL;
+    escape_graph* g = nullptr;
+    escape_status st;
+    if (dev_ptrs) {
+      int64_t* d_rp = nullptr;
+      e = cudaMalloc(&d_rp, sizeof(int64_t) * (n + 1));
+      if (e != cudaSuccess) return from_cuda(e);
+      k_rebase_rows<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(row_ptr + v0, n, e0, d_rp);
+      st = escape_load_csr(n, nnz, d_rp, col + e0, flags, stream, &g);
+      cudaFree(d_rp);
+    } else {
+      local.resize(n + 1);
+      for (int64_t i = 0; i <= n; ++i) local[i] = rp_host[v0 + i] - e0;
+      st = escape_load_csr(n, nnz, local.data(), col + e0, flags, stream, &g);
+    }
+    if (st != ESCAPE_OK) return st;
+    st = escape_census5(g, &res[k], stream);
+    escape_free(g);
+    if (st != ESCAPE_OK) return st;
+  }
+  memcpy(out, res.data(), sizeof(escape_census) * num_graphs);
+  return ESCAPE_OK;
+}
+
+escape_status escape_per_element(escape_graph* g, uint64_t* tri_e, uint64_t* c4_e, uint64_t* k4_e, uint64_t* tri_v,
+                                 uint64_t* c4_v, uint64_t* k4_v, void* stream) {
+  if (!g || !g->has_pe) return ESCAPE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long *dT = nullptr, *dC = nullptr, *dK = nullptr, *vt = nullptr, *vc = nullptr, *vk = nullptr;
+  size_t eb = sizeof(unsigned long long) * (g->nnz + 1), vb = sizeof(unsigned long long) * (g->n + 1);
+  cudaError_t e = cudaMalloc(&dT, eb);
+  if (e == cudaSuccess) e = cudaMalloc(&dC, eb);
+  if (e == cudaSuccess) e = cudaMalloc(&dK, eb);
+  if (e == cudaSuccess) e = cudaMalloc(&vt, vb);
+  if (e == cudaSuccess) e = cudaMalloc(&vc, vb);
+  if (e == cudaSuccess) e = cudaMalloc(&vk, vb);
+  if (e == cudaSuccess && g->n > 0) {
+    k_map_edges<<<(unsigned)std::min<int64_t>((g->n * 32 + 255) / 256, 65535), 256, 0, s>>>(
+        g->d_rp, g->d_col, g->n, g->ori.rank, g->ori.R, g->ori.C, g->pe.Te, g->pe.C4e, g->pe.K4e, dT, dC, dK);
+    k_map_vertices<<<(unsigned)std::min<int64_t>((g->n + 255) / 256, 65535), 256, 0, s>>>(
+        g->n, g->ori.rank, g->pe.tv, g->pe.C4v, g->pe.K4v, vt, vc, vk);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && tri_e && g->nnz) e = cudaMemcpyAsync(tri_e, dT, sizeof(uint64_t) * g->nnz, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && c4_e && g->nnz) e = cudaMemcpyAsync(c4_e, dC, sizeof(uint64_t) * g->nnz, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && k4_e && g->nnz) e = cudaMemcpyAsync(k4_e, dK, sizeof(uint64_t) * g->nnz, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && tri_v && g->n) e = cudaMemcpyAsync(tri_v, vt, sizeof(uint64_t) * g->n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && c4_v && g->n) e = cudaMemcpyAsync(c4_v, vc, sizeof(uint64_t) * g->n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && k4_v && g->n) e = cudaMemcpyAsync(k4_v, vk, sizeof(uint64_t) * g->n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dT); cudaFree(dC); cudaFree(dK); cudaFree(vt); cudaFree(vc); cudaFree(vk);
+  return from_cuda(e);
+}
+
+int escape_last_phase_ms(const escape_graph* g, float* ms, int count) {
+  if (!g) return 0;
+  int k = g->num_phases < count ? g->num_phases : count;
+  for (int i = 0; i < k && ms; ++i) ms[i] = g->phase_ms[i];
+  return g->num_phases;
+}
+
+void escape_free(escape_graph* g) {
+  if (!g) return;
+  free_pe(g);
+  cudaFree(g->d_rp);
+  cudaFree(g->d_col);
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+"""Write stored oracle results for the larger workloads (run from the repo root).
+
+Calls only the seeded generators and oracle/; every value written here comes
+from the CPU oracle.  Each file records a SHA-256 of the generated CSR so a
+test can tell whether the graph it regenerates is the one the values were
+computed for (and recompute them live if not).
+
+    python tests/golden/make_golden.py chung_lu er500
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import graphgen as gg  # noqa: E402
+import oracle  # noqa: E402
+from gpu_util import graph_hash  # noqa: E402
+
+
+WORKLOADS = {
+    "chung_lu": lambda: gg.config_chung_lu(1),
+    "er500": lambda: gg.config_er500(0),
+}
+
+
+def write(name):
+    g = WORKLOADS[name]()
+    t0 = time.time()
+    c = oracle.census(g)
+    out = {
+        "workload": name, "graph": g.name, "n": g.n, "m": g.m, "sha256": graph_hash(g),
+        "oracle_seconds": round(time.time() - t0, 1),
+        "c3": [str(x) for x in c["c3"]], "c4": [str(x) for x in c["c4"]], "c5": [str(x) for x in c["c5"]],
+        "n3": [str(x) for x in c["n3"]], "n4": [str(x) for x in c["n4"]], "n5": [str(x) for x in c["n5"]],
+        "sums": {k: str(v) for k, v in c["sums"].items()},
+    }
+    with open(os.path.join(HERE, f"census_{name}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, out["oracle_seconds"], "s")
+
+
+if __name__ == "__main__":
+    for name in sys.argv[1:] or list(WORKLOADS):
+        write(name)

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA census through the C ABI against the CPU oracle.
+
+Bar: bit-exact (all counts are integers).  Cases span several CTAs/tiles,
+ragged tails (out-degrees across the 32-lane and 64-bit word boundaries of the
+kernels), hub-heavy graphs, empty and tiny graphs, the ER(500) workload for
+ten seeds, the Chung-Lu workload (stored oracle result) and the R-MAT scale-22
+workload at full size (sampled per-element values and invariants).
+"""
+import json
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from gpu_util import assert_same_census, gpu_census
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    from paper_1610_09411_gb300 import build
+    build.build()
+
+
+# ------------------------------------------------------------------ small / structured
+
+def _structured():
+    return [gg.empty(0), gg.empty(1), gg.empty(4), gg.empty(9), gg.path(2), gg.path(4), gg.complete(4),
+            gg.complete(5), gg.complete(12), gg.star(6), gg.star(300), gg.cycle(5), gg.cycle(40),
+            gg.petersen(), gg.complete_bipartite(2, 3), gg.complete_bipartite(2, 70),
+            gg.complete_bipartite(5, 40),
+            gg.disjoint_union([gg.complete(6), gg.cycle(7), gg.star(9), gg.empty(3)])]
+
+
+@pytest.mark.parametrize("g", _structured(), ids=lambda g: f"{g.name}_n{g.n}")
+def test_structured_graphs_match_oracle(g):
+    assert_same_census(gpu_census(g), oracle.census(g))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_random_match_brute_force(seed):
+    g = [gg.erdos_renyi(14, 0.5, seed), gg.barabasi_albert(18, 3, seed), gg.chung_lu(24, 2.1, 6, 20, seed)][seed % 3]
+    got = gpu_census(g)
+    b = oracle.brute_census(g)
+    assert got["c5"] == b["c5"] and got["c4"] == b["c4"] and got["c3"] == b["c3"]
+
+
+@pytest.mark.parametrize("make", [
+    lambda: gg.complete(33),            # out-degrees 0..32: the 32-lane boundary
+    lambda: gg.complete(66),            # bit rows spanning two 64-bit words
+    lambda: gg.complete(131),           # three words, many 5-cliques
+    lambda: gg.erdos_renyi(400, 0.35, 1),
+    lambda: gg.erdos_renyi(3000, 0.01, 2),
+    lambda: gg.barabasi_albert(5000, 6, 3),
+    lambda: gg.chung_lu(20000, 2.1, 10, 2000, 4),
+    lambda: gg.rmat(12, 16, 0.57, 0.19, 0.19, 5),
+    lambda: gg.disjoint_union([gg.star(2000), gg.complete_bipartite(3, 500), gg.complete(40)]),
+], ids=["K33", "K66", "K131", "er400_dense", "er3000", "ba5000", "cl20000", "rmat12", "hubs"])
+def test_ragged_and_hub_graphs_match_oracle(make):
+    g = make()
+    assert_same_census(gpu_census(g), oracle.census(g))
+
+
+# ------------------------------------------------------------------ per-element arrays (Thm 7)
+
+@pytest.mark.parametrize("make", [lambda: gg.config_er500(3), lambda: gg.barabasi_albert(3000, 5, 1),
+                                  lambda: gg.chung_lu(20000, 2.1, 10, 2000, 4), lambda: gg.complete(70)],
+                         ids=["er500", "ba3000", "cl20000", "K70"])
+def test_per_element_arrays_match_oracle(make):
+    g = make()
+    got = gpu_census(g, per_element=True)["per_element"]
+    want = oracle.census(g, per_element=True)["per_element"]
+    for k in ("T_e", "t_i", "C4_e", "C4_i", "K4_e", "K4_i"):
+        assert np.array_equal(got[k], want[k]), k
+
+
+# ------------------------------------------------------------------ workloads
+
+@pytest.mark.parametrize("seed", range(10))
+def test_er500_workload(seed):
+    g = gg.config_er500(seed)
+    assert_same_census(gpu_census(g), oracle.census(g))
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"census_{name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+def test_chung_lu_workload():
+    """Chung-Lu n=262144, exponent 2.1, mean 16, clip 8192 (~2M edges)."""
+    from gpu_util import graph_hash
+    g = gg.config_chung_lu(1)
+    got = gpu_census(g, device=True)
+    gold = _golden("chung_lu")
+    if gold is not None and gold["sha256"] == graph_hash(g):
+        want = {k: [int(x) for x in gold[k]] for k in ("c3", "c4", "c5", "n3", "n4", "n5")}
+    else:   # the regenerated graph differs from the stored one: compute live
+        want = oracle.census(g)
+    assert_same_census(got, want)
+
+
+def test_device_and_host_pointers_agree():
+    g = gg.chung_lu(5000, 2.1, 8, 500, 7)
+    assert_same_census(gpu_census(g), gpu_census(g, device=True))
+
+
+def test_rmat_scale22_full_size_sampled():
+    """R-MAT scale 22 (the benchmark workload): per-element values at sampled
+    edges/vertices against the oracle's single-element definitions, and
+    invariants of the full census."""
+    g = gg.config_rmat()
+    got = gpu_census(g, per_element=True, device=True)
+    n = g.n
+    assert sum(got["c5"]) == comb(n, 5) and sum(got["c4"]) == comb(n, 4) and sum(got["c3"]) == comb(n, 3)
+    assert min(got["c5"] + got["c4"]) >= 0
+    pe = got["per_element"]
+    T = got["n3"][3]
+    assert int(pe["T_e"].sum()) == 6 * T and int(pe["t_i"].sum()) == 3 * T
+    assert int(pe["C4_e"].sum()) == 8 * got["n4"][3] and int(pe["C4_i"].sum()) == 4 * got["n4"][3]
+    assert int(pe["K4_e"].sum()) == 12 * got["n4"][5] and int(pe["K4_i"].sum()) == 4 * got["n4"][5]
+    rng = np.random.default_rng(2024)
+    src = np.repeat(np.arange(n), g.degrees())
+    idx = rng.choice(g.nnz, size=40, replace=False)
+    e = oracle.edge_elements(g, src[idx], g.col[idx])
+    for k in ("T_e", "K4_e", "C4_e"):
+        assert np.array_equal(pe[k][idx], e[k]), k
+    deg = g.degrees()
+    vs = rng.choice(np.nonzero((deg > 0) & (deg < 20000))[0], size=40, replace=False)
+    v = oracle.vertex_elements(g, vs)
+    for k in ("t_i", "C4_i"):
+        assert np.array_equal(pe[k][vs], v[k]), k
+
+
+# ------------------------------------------------------------------ input handling
+
+def test_normalize_flag_matches_clean_input():
+    from paper_1610_09411_gb300 import escape as esc
+    g = gg.erdos_renyi(200, 0.05, 9)
+    s, d = g.edges()
+    rng = np.random.default_rng(0)
+    # messy edge list: both/one direction, duplicates, self-loops, unsorted rows
+    us = np.concatenate([s, d[: len(d) // 2], s[:50], np.arange(30)])
+    vs = np.concatenate([d, s[: len(s) // 2], d[:50], np.arange(30)])
+    order = rng.permutation(len(us))
+    us, vs = us[order], vs[order]
+    cnt = np.bincount(us, minlength=g.n)
+    rp = np.zeros(g.n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(cnt)
+    col = vs[np.argsort(us, kind="stable")].astype(np.int32)
+    got = esc.census(rp, col, n=g.n, flags=esc.ESCAPE_NORMALIZE)
+    assert_same_census(got, oracle.census(g))
+
+
+@pytest.mark.parametrize("case", ["unsorted", "loop", "asymmetric", "out_of_range", "bad_rowptr"])
+def test_invalid_inputs_rejected(case):
+    from paper_1610_09411_gb300 import escape as esc
+    rp = np.array([0, 2, 4, 6], dtype=np.int64)
+    col = np.array([1, 2, 0, 2, 0, 1], dtype=np.int32)       # triangle
+    if case == "unsorted":
+        col = np.array([2, 1, 0, 2, 0, 1], dtype=np.int32)
+    elif case == "loop":
+        col = np.array([0, 1, 0, 2, 0, 1], dtype=np.int32)
+    elif case == "asymmetric":
+        rp = np.array([0, 2, 3, 5], dtype=np.int64)
+        col = np.array([1, 2, 0, 0, 1], dtype=np.int32)
+    elif case == "out_of_range":
+        col = np.array([1, 7, 0, 2, 0, 1], dtype=np.int32)
+    elif case == "bad_rowptr":
+        rp = np.array([0, 4, 2, 6], dtype=np.int64)
+    with pytest.raises(esc.EscapeError) as ei:
+        esc.escape_load_csr(3, rp, col)
+    assert ei.value.code == 1
+
+
+def test_batch_matches_single_graph_calls():
+    from paper_1610_09411_gb300 import escape as esc
+    graphs = gg.batch_graphs(12, 5, n_lo=20, n_hi=300)
+    voff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    rps, cols = [], []
+    base = 0
+    for k, g in enumerate(graphs):
+        voff[k + 1] = voff[k] + g.n
+        rps.append(g.row_ptr[:-1] + base)
+        cols.append(g.col)
+        base += g.nnz
+    rp = np.concatenate(rps + [np.array([base])]).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32)
+    res = esc.escape_census5_batch(voff, rp, col)
+    for g, r in zip(graphs, res):
+        assert_same_census(r, gpu_census(g))
+    assert_same_census(res[0], oracle.census(graphs[0]))

@@ -1,0 +1,349 @@
+"""Benchmark: exact 34-class 5-vertex census (plus 3-/4-vertex counts) of one
+synthetic graph per step, in edges per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload chung_lu|rmat22|er500]
+  python bench.py --impl reference ...     # the CPU oracle, timed on a bounded sample
+
+One step = one escape_census5 call on a graph already resident in HBM (its
+CSR loaded once before timing): orientation, every enumeration kernel and the
+128-bit assembly.  The L2 cache is flushed (256 MB write) between steps.
+N > 1 (torchrun) runs independent replicas, one per GPU: the census of one
+graph does not shard in this build (weak scaling, value = all ranks' edges /
+slowest rank's time).  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s for full 34-class induced 5-vertex census"
+UNIT = "edges/s"
+
+WORKLOADS = {
+    "chung_lu": "Chung-Lu power law n=262144, exponent 2.1, mean degree 16, max 8192, seed 1 (~2.0M edges)",
+    "rmat22": "R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), seed 1 (~64.2M edges)",
+    "er500": "Erdos-Renyi G(500, 0.012), seed 0",
+}
+# per-kernel algorithmic bytes: (phase, kernel, description, function of the oracle sums)
+ALG_BYTES = {
+    "wheels": ("k_wheels", "4 B x D (one id read per diamond, Thm 11 wheel sweep)", lambda s: 4 * s["D"]),
+    "pairs": ("k_pairs", "4 B x (W + D) (one id read per wedge and per diamond, Thms 11-12)",
+              lambda s: 4 * (s["W"] + s["D"])),
+    "cliques": ("k_clique_large", "4 B x (2 W++ + W+-) adjacency reads of the bit-matrix builds",
+                lambda s: None),
+    "cycles5": ("k_cycles5", "4 B x DP' (3-path endpoints)", lambda s: None),
+}
+
+
+def make_graph(name: str):
+    import graphgen as gg
+    if name == "chung_lu":
+        return gg.config_chung_lu(1)
+    if name == "rmat22":
+        return gg.config_rmat(22, 1)
+    if name == "er500":
+        return gg.config_er500(0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def oracle_sums(name: str, g):
+    """Counts the algorithmic-byte formulas need, as stored by the oracle
+    (tests/golden); None when no stored result matches this graph."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    try:
+        from gpu_util import graph_hash
+        path = os.path.join(ROOT, "tests", "golden", f"census_{name}.json")
+        if not os.path.exists(path):
+            return None
+        with open(path) as f:
+            gold = json.load(f)
+        if gold["sha256"] != graph_hash(g):
+            return None
+        return {k: int(v) for k, v in gold["sums"].items()}
+    except Exception:
+        return None
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    path = os.path.join(ROOT, "paper_1610_09411_gb300", "csrc", "census.cu")
+    with open(path, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        rec = t.get(f"{kernel}:{workload}")
+        if rec and rec.get("source_sha") == source_digest():
+            return rec["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(sample_n: int = 32768):
+    """The oracle as it stands, on a bounded sample of the workload: a Chung-Lu
+    graph of the same generator parameters and fewer vertices."""
+    import graphgen as gg
+    import oracle
+    g = gg.chung_lu(sample_n, 2.1, 16.0, 8192.0, 1)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.census(g)
+    dt = time.perf_counter() - t0
+    return {"value": g.m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Chung-Lu n={sample_n} (exponent 2.1, mean 16, clip 8192, seed 1), m={g.m}, full census, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import graphgen as gg
+    import oracle
+    oracle.build()
+    sample_n = 8192
+    g = gg.chung_lu(sample_n, 2.1, 16.0, 8192.0, 1)
+    for _ in range(args.warmup):
+        oracle.census(g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.census(g)
+    dt = time.perf_counter() - t0
+    value = g.m * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "sample": f"Chung-Lu n={sample_n} per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"Chung-Lu n={sample_n} (same generator), m={g.m}, full census per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chung_lu", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1610_09411_gb300 import build as pbuild
+    if rank == 0 or world == 1:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1610_09411_gb300 import escape as esc
+
+    g = make_graph(args.workload)
+    stream = torch.cuda.current_stream()
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    torch.cuda.synchronize()
+    h = esc.escape_load_csr(g.n, rp, col)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        res = esc.escape_census5(h)
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    phase_tot = {}
+    launches = 0
+    total_ms = 0.0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = esc.escape_census5(h)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        for k, v in esc.escape_last_phase_ms(h).items():
+            phase_tot[k] = phase_tot.get(k, 0.0) + v
+        launches += esc.escape_last_kernel_launches(h)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * g.m / (ms_per_step / 1000.0)
+
+    # end to end through the public C ABI with pinned host buffers: H2D of the
+    # CSR, the census, D2H of the result struct, every step
+    hrp = torch.from_numpy(g.row_ptr).pin_memory()
+    hcol = torch.from_numpy(g.col).pin_memory()
+    h2d = int(g.row_ptr.nbytes + g.col.nbytes)
+    d2h = 2 * 49 * 16
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh = esc.escape_load_csr(g.n, hrp.numpy(), hcol.numpy())
+        r2 = esc.escape_census5(hh)
+        esc.escape_free(hh)
+        e2e_ms += 1000 * (time.perf_counter() - t0)
+        assert r2["c5"] == res["c5"]
+    e2e_value = world * g.m / (e2e_ms / args.steps / 1000.0)
+    esc.escape_free(h)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the slowest phase with a byte model)
+    sums = oracle_sums(args.workload, g)
+    avg_phase = {k: v / args.steps for k, v in phase_tot.items()}
+    roof = None
+    cand = [(avg_phase.get(p, 0.0), p) for p in ALG_BYTES]
+    cand.sort(reverse=True)
+    peak, peak_src = measured_peak()
+    for ms, phase in cand:
+        kernel, desc, fn = ALG_BYTES[phase]
+        if sums is None or ms <= 0:
+            continue
+        b = fn(sums)
+        if b is None:
+            continue
+        achieved = b / (ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": stored_traffic(kernel, args.workload), "kernel": kernel, "phase_ms": ms,
+                "algorithmic_bytes": b, "bytes_model": desc, "peak_source": f"{peak_src} hbm_gbs"}
+        break
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": g.n, "m": g.m,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "phase_ms": {k: round(v, 3) for k, v in avg_phase.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -135,6 +135,9 @@ escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_
  */
 int escape_last_phase_ms(const escape_graph* g, float* ms, int count);
 
+/* Number of CUDA kernels the last escape_census5 call on this handle launched. */
+long long escape_last_kernel_launches(const escape_graph* g);
+
 void escape_free(escape_graph* g);
 
 /* Static string for a status code. */

@@ -1033,7 +1033,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
 
   const int TPB = 256;
-  if (n > 0) k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, acc);
+  if (n > 0) (k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, acc), note_launch());
 
   // ---------------- item lists for the out-neighbourhood passes
   DevBuf b_small, b_large, b_dims;
@@ -1042,8 +1042,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_dims.alloc(sizeof(unsigned long long) * 2));
   cudaMemsetAsync(b_dims.p, 0, sizeof(unsigned long long) * 2, s);
   if (n > 0) {
-    k_split_items<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), b_large.as<int32_t>(), ctr, SMALL_DPLUS);
-    k_clique_dims<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_dims.as<unsigned long long>());
+    (k_split_items<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), b_large.as<int32_t>(), ctr, SMALL_DPLUS), note_launch());
+    (k_clique_dims<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_dims.as<unsigned long long>()), note_launch());
   }
   unsigned long long hcnt[16] = {0}, dims[2] = {0, 0};
   cudaMemcpyAsync(hcnt, ctr, sizeof(hcnt), cudaMemcpyDeviceToHost, s);
@@ -1059,15 +1059,15 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   size_t smem_a = sizeof(int32_t) * (2 * (size_t)hcap_a) + sizeof(uint32_t) * dmax;
   int grid_sweep = sms * (cfg.cta_per_sm > 0 ? cfg.cta_per_sm : 1);
   if (nsmall > 0)
-    k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, acc);
+    (k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, acc), note_launch());
   if (nlarge > 0) {
     if (smem_a > 48 * 1024) ESC_TRY(cudaFuncSetAttribute(k_tri_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
-    k_tri_large<<<(unsigned)std::min<int64_t>(grid_sweep, nlarge), 512, smem_a, s>>>(
-        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, acc, hcap_a);
+    (k_tri_large<<<(unsigned)std::min<int64_t>(grid_sweep, nlarge), 512, smem_a, s>>>(
+        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, acc, hcap_a), note_launch());
   }
   if (n > 0) {
-    k_sym_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv);
-    k_vertex_from_edges_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv);
+    (k_sym_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv), note_launch());
+    (k_vertex_from_edges_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv), note_launch());
   }
   phase();
 
@@ -1097,11 +1097,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
     CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
     if (nitems > 0)
-      k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems), 512, smem_b, s>>>(
-          g, b_items.as<int32_t>(), nitems, ctr + 1, T, K4e, acc, cs, hcap, dmax, d_status);
+      (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems), 512, smem_b, s>>>(
+          g, b_items.as<int32_t>(), nitems, ctr + 1, T, K4e, acc, cs, hcap, dmax, d_status), note_launch());
     if (n > 0) {
-      k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e);
-      k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e, K4v, 3);
+      (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e), note_launch());
+      (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e, K4v, 3), note_launch());
     }
     ESC_TRY(cudaStreamSynchronize(s));   // b_items / b_D go out of scope
   }
@@ -1121,25 +1121,25 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
 
   // ---------------- 4-cycles (Thm 5)
   if (n > 0) {
-    k_cycles4<<<grid_sweep, 512, 0, s>>>(g, ctr + 2, ss, C4e, C4v, acc);
-    k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, C4e);
+    (k_cycles4<<<grid_sweep, 512, 0, s>>>(g, ctr + 2, ss, C4e, C4v, acc), note_launch());
+    (k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, C4e), note_launch());
   }
   phase();
 
   // ---------------- closed forms over vertices and edges
   if (n > 0)
-    k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, acc);
+    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, acc), note_launch());
 
   // ---------------- common-neighbour lists
   DevBuf b_off, b_U, b_bm;
   ESC_TRY(b_off.alloc(sizeof(int64_t) * (nnz + 2)));
   int64_t* off = b_off.as<int64_t>();
-  if (n > 0) k_canon_counts<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, off);
+  if (n > 0) (k_canon_counts<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, off), note_launch());
   ESC_TRY(exclusive_scan_i64(off, off, nnz, true, arena, s));
   int64_t ulen = 0;
   cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
-  if (n > 0) k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off);
+  if (n > 0) (k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off), note_launch());
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   int64_t bm_words = (n + 31) >> 5;
   ESC_TRY(b_bm.alloc(sizeof(uint32_t) * (size_t)bm_words * grid_sweep + 16));
@@ -1149,20 +1149,20 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
     ESC_TRY(cudaFuncSetAttribute(k_tri_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
     if (n > 0)
-      k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, T, b_U.as<int32_t>(), b_bm.as<uint32_t>(),
-                                                  hcap_l, d_status);
+      (k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, T, b_U.as<int32_t>(), b_bm.as<uint32_t>(),
+                                                  hcap_l, d_status), note_launch());
   }
   TriLists tl3{off, b_U.as<int32_t>()};
   phase();
 
   // ---------------- pairs: N13, N17 (Thms 11, 12)
-  if (n > 0) k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, acc);
+  if (n > 0) (k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, acc), note_launch());
   phase();
   // ---------------- wheels: N18 (Thm 11)
-  if (nnz > 0) k_wheels<<<grid_sweep, 512, 0, s>>>(g, ctr + 5, ss, tl3, T, acc);
+  if (nnz > 0) (k_wheels<<<grid_sweep, 512, 0, s>>>(g, ctr + 5, ss, tl3, T, acc), note_launch());
   phase();
   // ---------------- 5-cycles (Thm 13)
-  if (n > 0) k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, acc);
+  if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, acc), note_launch());
   phase();
 
   // ---------------- assembly
@@ -1170,7 +1170,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   conversion_inverse(3, tabs.a3);
   conversion_inverse(4, tabs.a4);
   conversion_inverse(5, tabs.a5);
-  k_assemble<<<1, 32, 0, s>>>(acc, (unsigned long long)n, (unsigned long long)(nnz / 2), tabs, d_out);
+  (k_assemble<<<1, 32, 0, s>>>(acc, (unsigned long long)n, (unsigned long long)(nnz / 2), tabs, d_out), note_launch());
   phase();
 
   if (pe_out) {

@@ -20,6 +20,7 @@ struct escape_graph {
   esc::Oriented ori;
   float phase_ms[9] = {0};
   int num_phases = 0;
+  long long launches = 0;     // kernels launched by the last census call
 };
 
 namespace {
@@ -137,6 +138,10 @@ long long embeddings(const Pat& small, const Pat& big, int k) {
 }  // namespace
 
 namespace esc {
+static thread_local long long g_launches = 0;
+void note_launch() { ++g_launches; }
+long long launches_so_far() { return g_launches; }
+
 // A[i][j] = (embeddings of pattern i into pattern j) / |Aut(pattern i)| = the
 // number of spanning subgraphs of pattern j isomorphic to pattern i; its
 // inverse by back-substitution (A is unit triangular when classes are ordered
@@ -375,8 +380,10 @@ escape_status escape_census5(escape_graph* g, escape_census* out, void* stream) 
   if (!g || !out) return ESCAPE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   free_pe(g);
+  long long l0 = esc::launches_so_far();
   escape_status st = census_one(g, g->d_rp, g->d_col, g->n, g->nnz, out, s, g->keep_pe != 0, &g->pe, &g->ori,
                                 g->phase_ms, &g->num_phases);
+  g->launches = esc::launches_so_far() - l0;
   if (st == ESCAPE_OK && g->keep_pe) g->has_pe = true;
   else free_pe(g);
   return st;
@@ -425,7 +432,7 @@ escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offset
       int64_t* d_rp = nullptr;
       e = cudaMalloc(&d_rp, sizeof(int64_t) * (n + 1));
       if (e != cudaSuccess) return from_cuda(e);
-      k_rebase_rows<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(row_ptr + v0, n, e0, d_rp);
+      (k_rebase_rows<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(row_ptr + v0, n, e0, d_rp), esc::note_launch());
       st = escape_load_csr(n, nnz, d_rp, col + e0, flags, stream, &g);
       cudaFree(d_rp);
     } else {
@@ -455,10 +462,10 @@ escape_status escape_per_element(escape_graph* g, uint64_t* tri_e, uint64_t* c4_
   if (e == cudaSuccess) e = cudaMalloc(&vc, vb);
   if (e == cudaSuccess) e = cudaMalloc(&vk, vb);
   if (e == cudaSuccess && g->n > 0) {
-    k_map_edges<<<(unsigned)std::min<int64_t>((g->n * 32 + 255) / 256, 65535), 256, 0, s>>>(
-        g->d_rp, g->d_col, g->n, g->ori.rank, g->ori.R, g->ori.C, g->pe.Te, g->pe.C4e, g->pe.K4e, dT, dC, dK);
-    k_map_vertices<<<(unsigned)std::min<int64_t>((g->n + 255) / 256, 65535), 256, 0, s>>>(
-        g->n, g->ori.rank, g->pe.tv, g->pe.C4v, g->pe.K4v, vt, vc, vk);
+    (k_map_edges<<<(unsigned)std::min<int64_t>((g->n * 32 + 255) / 256, 65535), 256, 0, s>>>(
+        g->d_rp, g->d_col, g->n, g->ori.rank, g->ori.R, g->ori.C, g->pe.Te, g->pe.C4e, g->pe.K4e, dT, dC, dK), esc::note_launch());
+    (k_map_vertices<<<(unsigned)std::min<int64_t>((g->n + 255) / 256, 65535), 256, 0, s>>>(
+        g->n, g->ori.rank, g->pe.tv, g->pe.C4v, g->pe.K4v, vt, vc, vk), esc::note_launch());
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && tri_e && g->nnz) e = cudaMemcpyAsync(tri_e, dT, sizeof(uint64_t) * g->nnz, cudaMemcpyDeviceToHost, s);
@@ -478,6 +485,8 @@ int escape_last_phase_ms(const escape_graph* g, float* ms, int count) {
   for (int i = 0; i < k && ms; ++i) ms[i] = g->phase_ms[i];
   return g->num_phases;
 }
+
+long long escape_last_kernel_launches(const escape_graph* g) { return g ? g->launches : 0; }
 
 void escape_free(escape_graph* g) {
   if (!g) return;

@@ -35,6 +35,10 @@ struct Oriented {
   int64_t* rev = nullptr;    // nnz
 };
 
+// Counts kernel launches made by this thread (reported per census call).
+void note_launch();
+long long launches_so_far();
+
 int bits_for(int64_t n);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, bool with_total, DeviceArena& arena,
                                cudaStream_t s);

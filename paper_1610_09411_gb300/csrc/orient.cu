@@ -93,20 +93,20 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, bool 
       // total = last exclusive + last input: computed by an extra reduce
       int64_t* sums = (int64_t*)arena.alloc(sizeof(int64_t));
       if (!sums) return cudaErrorMemoryAllocation;
-      k_scan_reduce<<<1, SCAN_BLOCK, 0, s>>>(in, n, sums);
-      k_scan_chunks<<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr);
+      (k_scan_reduce<<<1, SCAN_BLOCK, 0, s>>>(in, n, sums), note_launch());
+      (k_scan_chunks<<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr), note_launch());
       cudaMemcpyAsync(out + total_idx, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     } else {
-      k_scan_chunks<<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr);
+      (k_scan_chunks<<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr), note_launch());
     }
     return cudaGetLastError();
   }
   int64_t* sums = (int64_t*)arena.alloc(sizeof(int64_t) * (nb + 1));
   if (!sums) return cudaErrorMemoryAllocation;
-  k_scan_reduce<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, sums);
+  (k_scan_reduce<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, sums), note_launch());
   cudaError_t e = exclusive_scan_i64(sums, sums, nb, true, arena, s);
   if (e != cudaSuccess) return e;
-  k_scan_chunks<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, n, sums);
+  (k_scan_chunks<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, n, sums), note_launch());
   if (with_total) cudaMemcpyAsync(out + total_idx, sums + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   return cudaGetLastError();
 }
@@ -183,10 +183,10 @@ cudaError_t radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* t
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     int shift = p * 8;
-    k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, n, shift, ntiles, counts);
+    (k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, n, shift, ntiles, counts), note_launch());
     cudaError_t e = exclusive_scan_i64(counts, counts, RS_BINS * ntiles, false, arena, s);
     if (e != cudaSuccess) return e;
-    k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, ntiles, counts);
+    (k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, ntiles, counts), note_launch());
     uint64_t* t = ka; ka = kb; kb = t;
     uint32_t* t2 = va; va = vb; vb = t2;
   }
@@ -337,11 +337,11 @@ cudaError_t normalize_csr(int64_t n, int64_t nnz_in, const int64_t* rp_in, const
   uint64_t* tk = (uint64_t*)arena.alloc(sizeof(uint64_t) * (cnt + 1));
   int64_t* flag = (int64_t*)arena.alloc(sizeof(int64_t) * (cnt + 1));
   if (!keys || !tk || !flag) return cudaErrorMemoryAllocation;
-  if (cnt > 0) k_edge_keys_both<<<grid_for(nnz_in, 256, sms), 256, 0, s>>>(rp_in, col_in, n, nnz_in, vb, keys, d_status);
+  if (cnt > 0) (k_edge_keys_both<<<grid_for(nnz_in, 256, sms), 256, 0, s>>>(rp_in, col_in, n, nnz_in, vb, keys, d_status), note_launch());
   // keys use 2 vb bits plus the sentinel bit above them
   cudaError_t e = radix_sort(keys, nullptr, tk, nullptr, cnt, 2 * vb + 1, arena, s);
   if (e != cudaSuccess) return e;
-  if (cnt > 0) k_mark_unique<<<grid_for(cnt, 256, sms), 256, 0, s>>>(keys, cnt, vb, flag);
+  if (cnt > 0) (k_mark_unique<<<grid_for(cnt, 256, sms), 256, 0, s>>>(keys, cnt, vb, flag), note_launch());
   e = exclusive_scan_i64(flag, flag, cnt, true, arena, s);
   if (e != cudaSuccess) return e;
   int64_t nnz = 0;
@@ -354,7 +354,7 @@ cudaError_t normalize_csr(int64_t n, int64_t nnz_in, const int64_t* rp_in, const
   if (e == cudaSuccess) e = cudaMalloc(&col, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
   if (e != cudaSuccess) { cudaFree(rp); return e; }
   cudaMemsetAsync(rp, 0, sizeof(int64_t) * (n + 1), s);
-  if (cnt > 0) k_compact_csr<<<grid_for(cnt, 256, sms), 256, 0, s>>>(keys, flag, cnt, vb, col, rp);
+  if (cnt > 0) (k_compact_csr<<<grid_for(cnt, 256, sms), 256, 0, s>>>(keys, flag, cnt, vb, col, rp), note_launch());
   e = exclusive_scan_i64(rp, rp, n, true, arena, s);
   if (e != cudaSuccess) { cudaFree(rp); cudaFree(col); return e; }
   arena.release(mark);
@@ -366,7 +366,7 @@ cudaError_t normalize_csr(int64_t n, int64_t nnz_in, const int64_t* rp_in, const
 
 cudaError_t validate_csr(int64_t n, const int64_t* rp, const int32_t* col, unsigned* d_status, cudaStream_t s,
                          int sms) {
-  if (n > 0) k_validate<<<grid_for(n, 128, sms), 128, 0, s>>>(rp, col, n, d_status);
+  if (n > 0) (k_validate<<<grid_for(n, 128, sms), 128, 0, s>>>(rp, col, n, d_status), note_launch());
   return cudaGetLastError();
 }
 
@@ -382,26 +382,26 @@ cudaError_t orient(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz
   if (!keys || !tk || !vals || !tv) return cudaErrorMemoryAllocation;
   cudaError_t e;
   // 1. rank vertices by (degree, id): stable sort of degrees with ids as values
-  if (n > 0) k_degree_keys<<<grid_for(n, 256, sms), 256, 0, s>>>(rp, n, keys, vals);
+  if (n > 0) (k_degree_keys<<<grid_for(n, 256, sms), 256, 0, s>>>(rp, n, keys, vals), note_launch());
   int dbits = bits_for(nnz + 2);
   e = radix_sort(keys, vals, tk, tv, n, dbits, arena, s);
   if (e != cudaSuccess) return e;
-  if (n > 0) k_ranks<<<grid_for(n, 256, sms), 256, 0, s>>>(vals, keys, n, o.perm, o.rank, o.R);
+  if (n > 0) (k_ranks<<<grid_for(n, 256, sms), 256, 0, s>>>(vals, keys, n, o.perm, o.rank, o.R), note_launch());
   // 2. row starts in rank order
   e = exclusive_scan_i64(o.R, o.R, n, true, arena, s);
   if (e != cudaSuccess) return e;
   // 3. renamed entries sorted by (row rank, neighbour rank)
   int vb = bits_for(n > 1 ? n : 2);
   if (nnz > 0) {
-    k_rank_edge_keys<<<grid_for(n * 32, 256, sms), 256, 0, s>>>(rp, col, n, o.rank, vb, keys);
+    (k_rank_edge_keys<<<grid_for(n * 32, 256, sms), 256, 0, s>>>(rp, col, n, o.rank, vb, keys), note_launch());
     e = radix_sort(keys, nullptr, tk, nullptr, nnz, 2 * vb, arena, s);
     if (e != cudaSuccess) return e;
-    k_keys_to_col<<<grid_for(nnz, 256, sms), 256, 0, s>>>(keys, nnz, vb, o.C);
+    (k_keys_to_col<<<grid_for(nnz, 256, sms), 256, 0, s>>>(keys, nnz, vb, o.C), note_launch());
   }
   // 4. out-pointers and reverse slots
   if (n > 0) {
-    k_outptr<<<grid_for(n, 256, sms), 256, 0, s>>>(o.R, o.C, n, o.op);
-    k_rev<<<grid_for(n * 32, 256, sms), 256, 0, s>>>(o.R, o.C, n, o.rev);
+    (k_outptr<<<grid_for(n, 256, sms), 256, 0, s>>>(o.R, o.C, n, o.op), note_launch());
+    (k_rev<<<grid_for(n * 32, 256, sms), 256, 0, s>>>(o.R, o.C, n, o.rev), note_launch());
   }
   arena.release(mark);
   return cudaGetLastError();

@@ -66,6 +66,8 @@ def _load():
     lib.escape_set_options.argtypes = [P, c_int, c_int]
     lib.escape_last_phase_ms.restype = c_int
     lib.escape_last_phase_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), c_int]
+    lib.escape_last_kernel_launches.restype = ctypes.c_longlong
+    lib.escape_last_kernel_launches.argtypes = [P]
     lib.escape_free.restype = None
     lib.escape_free.argtypes = [P]
     lib.escape_status_str.restype = ctypes.c_char_p
@@ -185,6 +187,10 @@ def escape_last_phase_ms(h) -> dict:
     buf = (ctypes.c_float * N_PHASES)()
     k = LIB.escape_last_phase_ms(h, buf, N_PHASES)
     return {PHASE_NAMES[i]: float(buf[i]) for i in range(min(k, N_PHASES))}
+
+
+def escape_last_kernel_launches(h) -> int:
+    return int(LIB.escape_last_kernel_launches(h))
 
 
 def escape_free(h):

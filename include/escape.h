@@ -138,6 +138,32 @@ int escape_last_phase_ms(const escape_graph* g, float* ms, int count);
 /* Number of CUDA kernels the last escape_census5 call on this handle launched. */
 long long escape_last_kernel_launches(const escape_graph* g);
 
+/*
+ * escape_cycles4_noalloc -- per-vertex 4-cycle counts C4(i) and the total C4
+ * of a graph, computed without allocating any memory.  (The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the count -- for example a serving loop whose
+ * device memory is all handed to its own pool, or a latency-critical path that
+ * must not let cudaMalloc/cudaFree synchronise the device.)
+ *   n         number of vertices, 0 <= n <= ESCAPE_NOALLOC_MAX_N, else EOVERFLOW
+ *   row_ptr   DEVICE int64[n + 1], col DEVICE int32[row_ptr[n]]: a simple graph
+ *             as for escape_load_csr without NORMALIZE (sorted symmetric rows,
+ *             no self-loops); ids outside [0, n) are skipped and give EINVAL
+ *   c4_v      DEVICE uint64[n] output: 4-cycles through each vertex
+ *   c4_total  DEVICE uint64[1] output: number of 4-cycles
+ * Work space is one fixed device array of ESCAPE_NOALLOC_MAX_N x 64 words
+ * (8 MiB) inside the library, held by every GPU that loads the library until
+ * the process exits, and shared by every call: calls whose GPU work overlaps
+ * (on different streams or threads) race and must be serialised by the caller.
+ * Each call clears the work space and the outputs before counting.  The first
+ * call on a device looks up the array's device address (one-time set-up per
+ * device); make that first call before any stream capture.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ */
+#define ESCAPE_NOALLOC_MAX_N 32768
+escape_status escape_cycles4_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t* c4_v,
+                                     uint64_t* c4_total, void* stream);
+
 void escape_free(escape_graph* g);
 
 /* Static string for a status code. */

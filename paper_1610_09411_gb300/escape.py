@@ -68,6 +68,8 @@ def _load():
     lib.escape_last_phase_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), c_int]
     lib.escape_last_kernel_launches.restype = ctypes.c_longlong
     lib.escape_last_kernel_launches.argtypes = [P]
+    lib.escape_cycles4_noalloc.restype = c_int
+    lib.escape_cycles4_noalloc.argtypes = [i64, P, P, P, P, P]
     lib.escape_free.restype = None
     lib.escape_free.argtypes = [P]
     lib.escape_status_str.restype = ctypes.c_char_p
@@ -191,6 +193,19 @@ def escape_last_phase_ms(h) -> dict:
 
 def escape_last_kernel_launches(h) -> int:
     return int(LIB.escape_last_kernel_launches(h))
+
+
+def escape_cycles4_noalloc(n: int, row_ptr, col, c4_v, c4_total, stream=None):
+    """Per-vertex 4-cycle counts into caller-provided device tensors, with no
+    allocation inside the library (n <= ESCAPE_NOALLOC_MAX_N)."""
+    ptrs = [_ptr(a) for a in (row_ptr, col, c4_v, c4_total)]
+    if not all(dev for _, dev in ptrs):
+        raise ValueError("escape_cycles4_noalloc takes device tensors only")
+    _check(LIB.escape_cycles4_noalloc(int(n), ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], _stream(stream)),
+           "escape_cycles4_noalloc")
+
+
+ESCAPE_NOALLOC_MAX_N = 32768
 
 
 def escape_free(h):

@@ -508,15 +508,22 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
 // per-edge triangle lists).
 // ============================================================================
 struct TriLists {
-  const int64_t* off;   // per slot: start of the edge's common-neighbour list (both slots)
-  const int32_t* U;     // sorted common neighbours
+  const int64_t* off;    // per slot: start of the edge's id list (both slots of an edge share it)
+  const int32_t* U;      // sorted common-neighbour ids
+  const int64_t* offp;   // per slot: start of the slot's position list
+  const int32_t* P;      // per slot (u -> v): positions in row u of the common neighbours, ascending
 };
 
-__device__ __forceinline__ int64_t find_slot(const DevGraph& g, int64_t u, int32_t v) {
-  int64_t q = lower_bound_i32(g.C, g.R[u], g.R[u + 1], v);
-  return q;
-}
-
+// ============================================================================
+// Thm 11/12: N13 = sum_{j<i} C(W(i,j), 3) and
+// N17 = sum_{j<i} (W(i,j) - 2) cc(i,j), cc = edges inside N(i) cap N(j).
+// W(i,.) from every wedge i - c - j (c in N(i), j in N(c), j < i); C(W,3) is
+// accumulated on the fly as the sum of C(old, 2) over the increments.  The cc
+// term is gathered per diamond: for each triangle {i, x, y} (x < y, y reached
+// through the position list of (x, i), so its slot in row x is direct) and each
+// j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
+// per-edge triangle lists).
+// ============================================================================
 __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
                         Acc128* acc) {
   __shared__ u128 sh[32];
@@ -531,7 +538,7 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
     if (it < 0) break;
     int64_t i = g.n - 1 - it;
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
-    if (e0 == b0) continue;
+    if (e0 - b0 < 2) continue;
     if (threadIdx.x == 0) *nt = 0;
     __syncthreads();
     for (int64_t p = b0 + wid; p < e0; p += nw) {
@@ -539,22 +546,27 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
       int64_t cb = g.R[c], ce = g.rev[p];       // N(c) below i
       for (int64_t q = cb + lane; q < ce; q += 32) {
         int32_t j = g.C[q];
-        if (atomicAdd(&w[j], 1u) == 0) tl[atomicAdd(nt, 1u)] = j;
+        uint32_t old = atomicAdd(&w[j], 1u);
+        if (old == 0) tl[atomicAdd(nt, 1u)] = j;
+        else n13 += (u128)old * (old - 1) / 2;
       }
     }
     __syncthreads();
     unsigned ntc = *nt;
-    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) n13 += ch3(w[tl[t]]);
-    // diamonds with tip i: triangle (i, x, y), x < y, j in U(x,y), j < i
+    // diamonds with tip i
     for (int64_t p = b0 + wid; p < e0; p += nw) {
+      if (T[p] == 0) continue;
       int32_t x = g.C[p];
-      if (T[p] == 0) continue;                  // no triangle on (i, x)
-      int64_t ub = tl3.off[p], ue = ub + T[p];
-      for (int64_t r = ub; r < ue; ++r) {       // y in U(i,x), ascending
-        int32_t y = tl3.U[r];
-        if (y <= x) continue;
-        int64_t pxy = find_slot(g, x, y);
-        int64_t vb = tl3.off[pxy], ve = vb + T[pxy];
+      int64_t xb = g.R[x];
+      int32_t xo = (int32_t)(g.op[x] - xb);     // positions >= xo in row x are above x
+      int64_t rp_ = g.rev[p];                   // slot (x -> i)
+      const int32_t* ys = tl3.P + tl3.offp[rp_];
+      uint32_t ny = T[rp_];
+      for (uint32_t r = 0; r < ny; ++r) {
+        int32_t py = ys[r];
+        if (py < xo) continue;
+        int64_t sxy = xb + py;
+        int64_t vb = tl3.off[sxy], ve = vb + T[sxy];
         for (int64_t s = vb + lane; s < ve; s += 32) {
           int32_t j = tl3.U[s];
           if (j >= i) break;
@@ -577,51 +589,127 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
 // Thm 11: N18 (wheels) = sum over centres c of the 4-cycles of G[N(c)],
 // counted by the 4-cycle rule inside the neighbourhood: for u in N(c) and
 // v < u, C(w_c(u,v), 2) with w_c(u,v) = |{k in N(c) cap N(u) cap N(v): k < u}|.
-// Work items are (centre, one neighbour u); CTA-wide counters over v.
+// Everything happens in the position space of row c: the lists of the slots
+// (c -> u) hold positions in row c, so k < u is pk < pu and the counters are
+// indexed by position.  sum_v C(w, 2) is the sum of the values each increment
+// returns.
 // ============================================================================
-__global__ void k_wheels(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
-                         Acc128* acc) {
+static constexpr int WHEEL_WARP_MAX = 1024;     // centres up to this degree: one warp each
+
+__global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uint32_t* T, Acc128* acc) {
+  __shared__ u128 sh[32];
+  __shared__ uint32_t scr_all[8][WHEEL_WARP_MAX];
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  uint32_t* scr = scr_all[wl];
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  u128 n18 = 0;
+  for (int i = lane; i < WHEEL_WARP_MAX; i += 32) scr[i] = 0;
+  __syncwarp();
+  for (int64_t c = warp; c < c_end; c += nwarps) {
+    int64_t base = g.R[c];
+    int d = (int)(g.R[c + 1] - base);
+    if (d < 4) continue;
+    for (int pu = 0; pu < d; ++pu) {
+      uint32_t lenu = T[base + pu];
+      if (lenu < 2) continue;
+      const int32_t* Lu = tl3.P + tl3.offp[base + pu];
+      unsigned long long part = 0;
+      for (uint32_t a = 0; a < lenu; ++a) {
+        int32_t pk = Lu[a];
+        if (pk >= pu) break;
+        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
+        uint32_t lenk = T[base + pk];
+        for (uint32_t t = lane; t < lenk; t += 32) {
+          int32_t pv = Lk[t];
+          if (pv >= pu) break;
+          part += atomicAdd(&scr[pv], 1u);
+        }
+      }
+      __syncwarp();
+      for (uint32_t a = 0; a < lenu; ++a) {
+        int32_t pk = Lu[a];
+        if (pk >= pu) break;
+        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
+        uint32_t lenk = T[base + pk];
+        for (uint32_t t = lane; t < lenk; t += 32) {
+          int32_t pv = Lk[t];
+          if (pv >= pu) break;
+          scr[pv] = 0;
+        }
+      }
+      __syncwarp();
+      n18 += part;
+    }
+  }
+  LocalAcc<1> la;
+  la.v[0] = n18;
+  const int ids[1] = {ACC_N18};
+  flush_acc(la, ids, acc, sh);
+}
+
+// Centres above WHEEL_WARP_MAX: work items (centre, block of WHEEL_CHUNK
+// positions u); counters in shared memory when the degree fits, otherwise in a
+// per-CTA global region.
+static constexpr int WHEEL_CHUNK = 64;
+
+__global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, int64_t nitems,
+                             unsigned long long* qctr, TriLists tl3, const uint32_t* T, uint32_t* gscr,
+                             int64_t gscr_stride, int smem_cap, Acc128* acc) {
+  extern __shared__ uint32_t sscr[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
-  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
-  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   u128 n18 = 0;
+  bool zeroed_smem = false;
   while (true) {
-    // item = a slot p = (c -> u); slots in order
-    int64_t p = next_item(qctr, g.nnz, &sh_item);
-    if (p < 0) break;
-    uint32_t tcu = T[p];
-    if (tcu < 2) continue;
-    int32_t u = g.C[p];
-    // c = row of p: binary search over R (uniform across the block)
-    int64_t lo = 0, hi = g.n;
-    while (hi - lo > 1) { int64_t mid = (lo + hi) >> 1; if (g.R[mid] <= p) lo = mid; else hi = mid; }
-    int64_t c = lo;
-    if (threadIdx.x == 0) *nt = 0;
-    __syncthreads();
-    int64_t ub = tl3.off[p];
-    // k in U(c,u) with k < u
-    for (int64_t r = ub + wid; r < ub + tcu; r += nw) {
-      int32_t k = tl3.U[r];
-      if (k >= u) break;
-      int64_t pck = find_slot(g, c, k);
-      int64_t vb = tl3.off[pck], ve = vb + T[pck];
-      for (int64_t s = vb + lane; s < ve; s += 32) {
-        int32_t v = tl3.U[s];
-        if (v >= u) break;
-        if (atomicAdd(&w[v], 1u) == 0) tl[atomicAdd(nt, 1u)] = v;
+    int64_t it = next_item(qctr, nitems, &sh_item);
+    if (it < 0) break;
+    // centre of item `it`: the last k with item_off[k] <= it (item_off over centres c0..n-1)
+    int64_t lo = 0, hi = g.n - c0;
+    while (hi - lo > 1) { int64_t mid = (lo + hi) >> 1; if (item_off[mid] <= it) lo = mid; else hi = mid; }
+    int64_t c = c0 + lo;
+    int64_t base = g.R[c];
+    int d = (int)(g.R[c + 1] - base);
+    int u0 = (int)(it - item_off[lo]) * WHEEL_CHUNK;
+    int u1 = min(d, u0 + WHEEL_CHUNK);
+    uint32_t* scr = d <= smem_cap ? sscr : gscr + (int64_t)blockIdx.x * gscr_stride;
+    if (d <= smem_cap && !zeroed_smem) {
+      for (int i = threadIdx.x; i < smem_cap; i += blockDim.x) sscr[i] = 0;
+      zeroed_smem = true;
+      __syncthreads();
+    }
+    for (int pu = u0; pu < u1; ++pu) {
+      uint32_t lenu = T[base + pu];
+      if (lenu < 2) continue;
+      const int32_t* Lu = tl3.P + tl3.offp[base + pu];
+      unsigned long long part = 0;
+      for (uint32_t a = wid; a < lenu; a += nw) {
+        int32_t pk = Lu[a];
+        if (pk >= pu) break;
+        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
+        uint32_t lenk = T[base + pk];
+        for (uint32_t t = lane; t < lenk; t += 32) {
+          int32_t pv = Lk[t];
+          if (pv >= pu) break;
+          part += atomicAdd(&scr[pv], 1u);
+        }
       }
+      n18 += part;
+      __syncthreads();
+      for (uint32_t a = wid; a < lenu; a += nw) {
+        int32_t pk = Lu[a];
+        if (pk >= pu) break;
+        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
+        uint32_t lenk = T[base + pk];
+        for (uint32_t t = lane; t < lenk; t += 32) {
+          int32_t pv = Lk[t];
+          if (pv >= pu) break;
+          scr[pv] = 0;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    unsigned ntc = *nt;
-    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) {
-      int32_t v = tl[t];
-      n18 += ch2(w[v]);
-      w[v] = 0;
-    }
-    __syncthreads();
   }
   LocalAcc<1> la;
   la.v[0] = n18;
@@ -696,18 +784,19 @@ __global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
 
 // ============================================================================
 // Per-edge common-neighbour lists (the per-edge triangle lists of Thm 7),
-// sorted ascending, stored once per undirected edge and addressed from both
-// slots.  Built per higher endpoint y: N(y) goes into a membership table, and
-// for every lower neighbour x the row N(x) is filtered through it.
+// stored sorted: the id list once per undirected edge (addressed from both
+// slots), and for each slot (u -> v) the positions in row u of the same
+// vertices.  Built per higher endpoint y: N(y) goes into a hash table (vertex
+// -> position in row y), and for every lower neighbour x the row N(x) is
+// filtered through it; a hit at index q of row x has position q - R[x] there.
 // ============================================================================
-__global__ void k_tri_lists(DevGraph g, unsigned long long* qctr, const int64_t* off, const uint32_t* T, int32_t* U,
-                            uint32_t* bitmap_all, int hash_cap, unsigned* status) {
+__global__ void k_tri_lists(DevGraph g, unsigned long long* qctr, const int64_t* off, const int64_t* offp,
+                            const uint32_t* T, int32_t* U, int32_t* P, int32_t* ghash, int64_t ghash_cap,
+                            int hash_cap, unsigned* status) {
   extern __shared__ int32_t smem[];
   __shared__ int64_t sh_item;
-  int32_t* hk = smem;
-  int32_t* hv = hk + hash_cap;
-  uint32_t* bm = bitmap_all + (int64_t)blockIdx.x * ((g.n + 31) >> 5);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t* gk = ghash + (int64_t)blockIdx.x * 2 * ghash_cap;
   while (true) {
     int64_t it = next_item(qctr, g.n, &sh_item);
     if (it < 0) break;
@@ -716,48 +805,44 @@ __global__ void k_tri_lists(DevGraph g, unsigned long long* qctr, const int64_t*
     if (yo == yb) continue;
     int dy = (int)(ye - yb);
     bool small = 2 * dy <= hash_cap;
-    int hsz = small ? pow2_at_least(2 * dy) : 0;
-    PosHash H{hk, hv, hsz - 1};
-    if (small) {
-      for (int i = threadIdx.x; i < hsz; i += blockDim.x) hk[i] = -1;
-      __syncthreads();
-      for (int i = threadIdx.x; i < dy; i += blockDim.x) H.insert(g.C[yb + i], i);
-    } else {
-      for (int64_t p = yb + threadIdx.x; p < ye; p += blockDim.x) {
-        int32_t v = g.C[p];
-        atomicOr(&bm[v >> 5], 1u << (v & 31));
-      }
+    int hsz = pow2_at_least(2 * dy);
+    if (!small && hsz > ghash_cap) {            // cannot happen: sized by the maximum degree
+      if (threadIdx.x == 0) set_err(status, DEVERR_SCRATCH);
+      continue;
     }
+    PosHash H = small ? PosHash{smem, smem + hash_cap, hsz - 1} : PosHash{gk, gk + ghash_cap, hsz - 1};
+    for (int i = threadIdx.x; i < hsz; i += blockDim.x) H.keys[i] = -1;
     __syncthreads();
-    for (int64_t p = yb + wid; p < yo; p += nw) {   // x in N-(y)
+    for (int i = threadIdx.x; i < dy; i += blockDim.x) H.insert(g.C[yb + i], i);
+    __syncthreads();
+    for (int64_t p = yb + wid; p < yo; p += nw) {   // x in N-(y); p = slot (y -> x)
       int32_t x = g.C[p];
       int64_t cs = g.rev[p];                        // canonical slot (x -> y)
-      int64_t out = off[cs];
+      int64_t out = off[cs], outx = offp[cs], outy = offp[p];
       uint32_t expect = T[cs];
       uint32_t written = 0;
-      for (int64_t base = g.R[x]; base < g.R[x + 1]; base += 32) {
+      int64_t xb = g.R[x];
+      for (int64_t base = xb; base < g.R[x + 1]; base += 32) {
         int64_t q = base + lane;
-        bool hit = false;
-        int32_t z = -1;
+        int32_t py = -1, z = -1;
         if (q < g.R[x + 1]) {
           z = g.C[q];
-          hit = small ? (H.find(z) >= 0) : ((bm[z >> 5] >> (z & 31)) & 1u);
+          py = H.find(z);
         }
+        bool hit = py >= 0;
         unsigned hm = __ballot_sync(0xffffffffu, hit);
         if (hit) {
           unsigned k = written + __popc(hm & ((1u << lane) - 1u));
-          if (k < expect) U[out + k] = z;
+          if (k < expect) {
+            U[out + k] = z;
+            P[outx + k] = (int32_t)(q - xb);
+            P[outy + k] = py;
+          }
         }
         written += __popc(hm);
       }
       if (lane == 0 && written != expect) set_err(status, DEVERR_BOUNDS);
     }
-    __syncthreads();
-    if (!small)
-      for (int64_t p = yb + threadIdx.x; p < ye; p += blockDim.x) {
-        int32_t v = g.C[p];
-        atomicAnd(&bm[v >> 5], ~(1u << (v & 31)));
-      }
     __syncthreads();
   }
 }
@@ -771,6 +856,10 @@ __global__ void k_canon_counts(DevGraph g, const uint32_t* T, int64_t* cnt) {
     for (int64_t p = g.R[v] + lane; p < g.op[v]; p += 32) cnt[p] = 0;
     for (int64_t p = g.op[v] + lane; p < g.R[v + 1]; p += 32) cnt[p] = T[p];
   }
+}
+__global__ void k_all_counts(const uint32_t* T, int64_t nnz, int64_t* cnt) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) cnt[p] = T[p];
 }
 __global__ void k_share_offsets(DevGraph g, int64_t* off) {
   int lane = threadIdx.x & 31;
@@ -1130,36 +1219,89 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (n > 0)
     (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, acc), note_launch());
 
-  // ---------------- common-neighbour lists
-  DevBuf b_off, b_U, b_bm;
+  // ---------------- common-neighbour lists: ids (canonical) and positions (per slot)
+  DevBuf b_off, b_offp, b_U, b_P, b_gh;
   ESC_TRY(b_off.alloc(sizeof(int64_t) * (nnz + 2)));
+  ESC_TRY(b_offp.alloc(sizeof(int64_t) * (nnz + 2)));
   int64_t* off = b_off.as<int64_t>();
+  int64_t* offp = b_offp.as<int64_t>();
   if (n > 0) (k_canon_counts<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, off), note_launch());
   ESC_TRY(exclusive_scan_i64(off, off, nnz, true, arena, s));
-  int64_t ulen = 0;
+  if (n > 0) (k_all_counts<<<grid_for(nnz, TPB, sms), TPB, 0, s>>>(T, nnz, offp), note_launch());
+  ESC_TRY(exclusive_scan_i64(offp, offp, nnz, true, arena, s));
+  int64_t ulen = 0, plen = 0;
   cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&plen, offp + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
   if (n > 0) (k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off), note_launch());
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
-  int64_t bm_words = (n + 31) >> 5;
-  ESC_TRY(b_bm.alloc(sizeof(uint32_t) * (size_t)bm_words * grid_sweep + 16));
-  cudaMemsetAsync(b_bm.p, 0, sizeof(uint32_t) * (size_t)bm_words * grid_sweep + 16, s);
+  ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
+  int64_t maxdeg = 0;
   {
-    int hcap_l = 8192;
+    int64_t last[2] = {0, 0};
+    if (n > 0) {
+      cudaMemcpyAsync(last, o.R + n - 1, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s);
+      ESC_TRY(cudaStreamSynchronize(s));
+    }
+    maxdeg = last[1] - last[0];                  // the highest rank has the largest degree
+  }
+  const int hcap_l = 8192;
+  int64_t ghash_cap = pow2_at_least((int)std::max<int64_t>(2 * maxdeg, 2));
+  if (2 * maxdeg <= hcap_l) ghash_cap = 2;
+  ESC_TRY(b_gh.alloc(sizeof(int32_t) * 2 * (size_t)ghash_cap * grid_sweep + 16));
+  {
     size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
     ESC_TRY(cudaFuncSetAttribute(k_tri_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
     if (n > 0)
-      (k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, T, b_U.as<int32_t>(), b_bm.as<uint32_t>(),
-                                                  hcap_l, d_status), note_launch());
+      (k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, offp, T, b_U.as<int32_t>(), b_P.as<int32_t>(),
+                                                   b_gh.as<int32_t>(), ghash_cap, hcap_l, d_status), note_launch());
   }
-  TriLists tl3{off, b_U.as<int32_t>()};
+  TriLists tl3{off, b_U.as<int32_t>(), offp, b_P.as<int32_t>()};
   phase();
 
   // ---------------- pairs: N13, N17 (Thms 11, 12)
   if (n > 0) (k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, acc), note_launch());
   phase();
   // ---------------- wheels: N18 (Thm 11)
-  if (nnz > 0) (k_wheels<<<grid_sweep, 512, 0, s>>>(g, ctr + 5, ss, tl3, T, acc), note_launch());
+  {
+    // centres by degree: ranks are in degree order, so the large centres are a suffix
+    int64_t c0 = n;
+    if (n > 0) {
+      std::vector<int64_t> hR(n + 1);
+      cudaMemcpyAsync(hR.data(), o.R, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s);
+      ESC_TRY(cudaStreamSynchronize(s));
+      int64_t lo = 0, hi = n;                    // first rank with degree > WHEEL_WARP_MAX
+      while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] > WHEEL_WARP_MAX) hi = mid; else lo = mid + 1; }
+      c0 = lo;
+      if (c0 > 0)
+        (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s>>>(g, c0, tl3, T, acc), note_launch());
+      if (c0 < n) {
+        std::vector<int64_t> item_off(n - c0 + 1);
+        item_off[0] = 0;
+        for (int64_t c = c0; c < n; ++c)
+          item_off[c - c0 + 1] = item_off[c - c0] + (hR[c + 1] - hR[c] + WHEEL_CHUNK - 1) / WHEEL_CHUNK;
+        int64_t nitems = item_off[n - c0];
+        DevBuf b_io, b_gs;
+        ESC_TRY(b_io.alloc(sizeof(int64_t) * (n - c0 + 1)));
+        cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int smem_optin = 0;
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int smem_cap = std::max(0, (smem_optin - 4096) / 4);
+        smem_cap = std::min<int64_t>(smem_cap, maxdeg);
+        int blocks = sms;
+        int64_t gstride = maxdeg > smem_cap ? maxdeg : 1;
+        ESC_TRY(b_gs.alloc(sizeof(uint32_t) * (size_t)gstride * blocks + 16));
+        cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * blocks + 16, s);
+        size_t smem_w = sizeof(uint32_t) * (size_t)std::max(smem_cap, 1);
+        ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
+        (k_wheels_cta<<<blocks, 512, smem_w, s>>>(g, c0, b_io.as<int64_t>(), nitems, ctr + 5, tl3, T,
+                                                  b_gs.as<uint32_t>(), gstride, smem_cap, acc), note_launch());
+        ESC_TRY(cudaStreamSynchronize(s));
+      }
+    }
+  }
   phase();
   // ---------------- 5-cycles (Thm 13)
   if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, acc), note_launch());

@@ -61,11 +61,12 @@ static __host__ __device__ __forceinline__ int pow2_at_least(int x) {
 // Degree sums (Thm 4, Thm 8 N1/N3, Thm 9 N2, App. A P3+K2 terms).
 // One warp per vertex.
 // ============================================================================
-__global__ void k_vertex_basic(DevGraph g, Acc128* acc) {
+__global__ void k_vertex_basic(DevGraph g, AccSet acc) {
   __shared__ u128 sh[32];
   int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ids[8] = {ACC_W, ACC_S3, ACC_S4, ACC_D2D, ACC_DNBR, ACC_N2A, ACC_N3A, ACC_P4A};
   LocalAcc<8> la;
   la.zero();
   for (int64_t v = warp; v < g.n; v += nwarps) {
@@ -95,9 +96,9 @@ __global__ void k_vertex_basic(DevGraph g, Acc128* acc) {
       la.v[6] += (s1 * s1 - s2) / 2;
       la.v[7] += p4a;
     }
+    warp_item_flush(la, ids, acc, v);
   }
-  const int ids[8] = {ACC_W, ACC_S3, ACC_S4, ACC_D2D, ACC_DNBR, ACC_N2A, ACC_N3A, ACC_P4A};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // ============================================================================
@@ -111,13 +112,14 @@ static constexpr int SMALL_DPLUS = 32;    // warp-per-vertex path up to this out
 
 // Warp per vertex with d+ <= 32: N+(x) in a per-warp shared-memory list,
 // membership by binary search.
-__global__ void k_tri_small(DevGraph g, const int32_t* items, int64_t nitems, uint32_t* T, Acc128* acc) {
+__global__ void k_tri_small(DevGraph g, const int32_t* items, int64_t nitems, uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int32_t lst[8][SMALL_DPLUS];
   __shared__ uint32_t cnt[8][SMALL_DPLUS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ids[2] = {ACC_T, ACC_N8Z};
   LocalAcc<2> la;
   la.zero();
   for (int64_t it = warp; it < nitems; it += nwarps) {
@@ -148,14 +150,14 @@ __global__ void k_tri_small(DevGraph g, const int32_t* items, int64_t nitems, ui
     __syncwarp();
     if (lane < d && cnt[wl][lane]) atomicAdd(&T[o + lane], cnt[wl][lane]);
     __syncwarp();
+    warp_item_flush(la, ids, acc, x);
   }
-  const int ids[2] = {ACC_T, ACC_N8Z};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // CTA per vertex with d+ > 32: N+(x) in a shared-memory hash.
 __global__ void k_tri_large(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
-                            uint32_t* T, Acc128* acc, int hash_cap) {
+                            uint32_t* T, AccSet acc, int hash_cap) {
   extern __shared__ int32_t smem[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
@@ -163,6 +165,7 @@ __global__ void k_tri_large(DevGraph g, const int32_t* items, int64_t nitems, un
   int32_t* hv = hk + hash_cap;
   uint32_t* cnt = (uint32_t*)(hv + hash_cap);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ids[2] = {ACC_T, ACC_N8Z};
   LocalAcc<2> la;
   la.zero();
   while (true) {
@@ -201,10 +204,10 @@ __global__ void k_tri_large(DevGraph g, const int32_t* items, int64_t nitems, un
     __syncthreads();
     for (int i = threadIdx.x; i < d; i += blockDim.x)
       if (cnt[i]) atomicAdd(&T[o + i], cnt[i]);
+    block_item_flush(la, ids, acc, x, sh);
     __syncthreads();
   }
-  const int ids[2] = {ACC_T, ACC_N8Z};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // Copy canonical per-edge values to the reverse slot; per-vertex sums.
@@ -322,7 +325,7 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int
 // Shared-memory layout for the CTA path: hash (2 x hcap ints), nb values,
 // B (d x W u64), K4 accumulators (d u64), T of x's out-edges (d u32).
 __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
-                               const uint32_t* T, unsigned long long* K4e, Acc128* acc, CliqueScratch cs,
+                               const uint32_t* T, unsigned long long* K4e, AccSet acc, CliqueScratch cs,
                                int hash_cap, int dmax, unsigned* status) {
   extern __shared__ uint64_t smem64[];
   __shared__ u128 sh[32];
@@ -335,7 +338,8 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
   uint32_t* Tx = (uint32_t*)(hv + hash_cap);                   // dmax
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint64_t* D = cs.D + (int64_t)blockIdx.x * cs.d_words;
-  LocalAcc<7> la;
+  const int ids[5] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21};
+  LocalAcc<5> la;
   la.zero();
   while (true) {
     int64_t it = next_item(qctr, nitems, &sh_item);
@@ -416,12 +420,10 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
     __syncthreads();
     for (int i = threadIdx.x; i < d; i += blockDim.x)
       if (k4x[i]) atomicAdd(&K4e[o + i], k4x[i] / 2);
+    block_item_flush(la, ids, acc, x, sh);
     __syncthreads();
   }
-  const int ids[5] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21};
-  LocalAcc<5> l5;
-  for (int i = 0; i < 5; ++i) l5.v[i] = la.v[i];
-  flush_acc(l5, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // ============================================================================
@@ -441,7 +443,7 @@ struct SweepScratch {
 };
 
 __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss, unsigned long long* C4raw,
-                          unsigned long long* C4v, Acc128* acc) {
+                          unsigned long long* C4v, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
@@ -477,7 +479,8 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
     u128 tot = block_sum_u128(mine, sh);
     if (threadIdx.x == 0) {
       if (tot) atomicAdd(&C4v[i], (unsigned long long)tot);
-      c4sum += tot;
+      if (acc.vg) acc_add(acc_of(acc, i), ACC_C4, tot);
+      else c4sum += tot;
     }
     // pass 3: per-edge counts
     for (int64_t p = b0 + wid; p < e0; p += nw) {
@@ -496,7 +499,7 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
     for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
     __syncthreads();
   }
-  if (threadIdx.x == 0) acc_add(acc, ACC_C4, c4sum);
+  if (threadIdx.x == 0 && !acc.vg) acc_add(acc.base, ACC_C4, c4sum);
 }
 
 // ============================================================================
@@ -525,20 +528,23 @@ struct TriLists {
 // per-edge triangle lists).
 // ============================================================================
 __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
-                        Acc128* acc) {
+                        AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
   int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
   unsigned* nt = ss.ntouched + 2 * blockIdx.x;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  u128 n13 = 0, n17 = 0;
+  const int ids[2] = {ACC_N13, ACC_N17};
+  LocalAcc<2> la;
+  la.zero();
   while (true) {
     int64_t it = next_item(qctr, g.n, &sh_item);
     if (it < 0) break;
     int64_t i = g.n - 1 - it;
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
     if (e0 - b0 < 2) continue;
+    u128 n13 = 0, n17 = 0;
     if (threadIdx.x == 0) *nt = 0;
     __syncthreads();
     for (int64_t p = b0 + wid; p < e0; p += nw) {
@@ -576,13 +582,12 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
     }
     __syncthreads();
     for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
+    la.v[0] += n13;
+    la.v[1] += n17;
+    block_item_flush(la, ids, acc, i, sh);
     __syncthreads();
   }
-  LocalAcc<2> la;
-  la.v[0] = n13;
-  la.v[1] = n17;
-  const int ids[2] = {ACC_N13, ACC_N17};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // ============================================================================
@@ -596,20 +601,23 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
 // ============================================================================
 static constexpr int WHEEL_WARP_MAX = 1024;     // centres up to this degree: one warp each
 
-__global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uint32_t* T, Acc128* acc) {
+__global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ uint32_t scr_all[8][WHEEL_WARP_MAX];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   uint32_t* scr = scr_all[wl];
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  u128 n18 = 0;
+  const int ids[1] = {ACC_N18};
+  LocalAcc<1> la;
+  la.zero();
   for (int i = lane; i < WHEEL_WARP_MAX; i += 32) scr[i] = 0;
   __syncwarp();
   for (int64_t c = warp; c < c_end; c += nwarps) {
     int64_t base = g.R[c];
     int d = (int)(g.R[c + 1] - base);
     if (d < 4) continue;
+    u128 n18 = 0;
     for (int pu = 0; pu < d; ++pu) {
       uint32_t lenu = T[base + pu];
       if (lenu < 2) continue;
@@ -641,11 +649,10 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uin
       __syncwarp();
       n18 += part;
     }
+    la.v[0] += n18;
+    warp_item_flush(la, ids, acc, c);
   }
-  LocalAcc<1> la;
-  la.v[0] = n18;
-  const int ids[1] = {ACC_N18};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // Centres above WHEEL_WARP_MAX: work items (centre, block of WHEEL_CHUNK
@@ -655,12 +662,14 @@ static constexpr int WHEEL_CHUNK = 64;
 
 __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, int64_t nitems,
                              unsigned long long* qctr, TriLists tl3, const uint32_t* T, uint32_t* gscr,
-                             int64_t gscr_stride, int smem_cap, Acc128* acc) {
+                             int64_t gscr_stride, int smem_cap, AccSet acc) {
   extern __shared__ uint32_t sscr[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  u128 n18 = 0;
+  const int ids[1] = {ACC_N18};
+  LocalAcc<1> la;
+  la.zero();
   bool zeroed_smem = false;
   while (true) {
     int64_t it = next_item(qctr, nitems, &sh_item);
@@ -695,7 +704,7 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
           part += atomicAdd(&scr[pv], 1u);
         }
       }
-      n18 += part;
+      la.v[0] += part;
       __syncthreads();
       for (uint32_t a = wid; a < lenu; a += nw) {
         int32_t pk = Lu[a];
@@ -710,11 +719,9 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
       }
       __syncthreads();
     }
+    block_item_flush(la, ids, acc, c, sh);
   }
-  LocalAcc<1> la;
-  la.v[0] = n18;
-  const int ids[1] = {ACC_N18};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // ============================================================================
@@ -725,7 +732,7 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
 // The paths whose own a or b is counted by w' are the directed tailed
 // triangles, subtracted through ACC_N8Z (pass A).
 // ============================================================================
-__global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss, Acc128* acc) {
+__global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   uint32_t* wp = ss.cnt + (int64_t)blockIdx.x * ss.n;
@@ -734,7 +741,9 @@ __global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
   int32_t* tl2 = ss.touched2 + (int64_t)blockIdx.x * ss.n;
   unsigned* nt = ss.ntouched + 2 * blockIdx.x;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  u128 m = 0;
+  const int ids[1] = {ACC_N8M};
+  LocalAcc<1> la;
+  la.zero();
   while (true) {
     int64_t it = next_item(qctr, g.n, &sh_item);
     if (it < 0) break;
@@ -769,17 +778,15 @@ __global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       unsigned long long s = 0;
       for (int64_t q = g.op[b] + lane; q < g.R[b + 1]; q += 32) s += wp[g.C[q]];
       s = warp_sum_u64(s);
-      if (lane == 0) m += (u128)s * p2[b];
+      if (lane == 0) la.v[0] += (u128)s * p2[b];
     }
     __syncthreads();
     for (unsigned t = threadIdx.x; t < n1; t += blockDim.x) wp[tl[t]] = 0;
     for (unsigned t = threadIdx.x; t < n2; t += blockDim.x) p2[tl2[t]] = 0;
+    block_item_flush(la, ids, acc, i, sh);
     __syncthreads();
   }
-  LocalAcc<1> la;
-  la.v[0] = m;
-  const int ids[1] = {ACC_N8M};
-  flush_acc(la, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // ============================================================================
@@ -875,12 +882,14 @@ __global__ void k_share_offsets(DevGraph g, int64_t* off) {
 // ============================================================================
 __global__ void k_edge_sums(DevGraph g, const uint32_t* T, const unsigned long long* C4e,
                             const unsigned long long* K4e, const unsigned long long* tv,
-                            const unsigned long long* C4v, const unsigned long long* K4v, Acc128* acc) {
+                            const unsigned long long* C4v, const unsigned long long* K4v, AccSet acc) {
   __shared__ u128 sh[32];
   int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  LocalAcc<16> la;
+  const int ids[13] = {ACC_N5A, ACC_N11, ACC_D, ACC_N14, ACC_N6A, ACC_N12A, ACC_N19,
+                       ACC_TT, ACC_N4, ACC_N9A, ACC_N7A, ACC_N15, ACC_TD};
+  LocalAcc<13> la;
   la.zero();
   for (int64_t v = warp; v < g.n; v += nwarps) {
     unsigned long long dv = (unsigned long long)dg_deg(g, v), tvv = tv[v];
@@ -906,12 +915,9 @@ __global__ void k_edge_sums(DevGraph g, const uint32_t* T, const unsigned long l
       if (K4v[v]) la.v[11] += (u128)K4v[v] * (dv - 3);              // N15
       la.v[12] += (u128)tvv * dv;                                   // P3+K2 / K3+K2 terms
     }
+    warp_item_flush(la, ids, acc, v);
   }
-  const int ids[13] = {ACC_N5A, ACC_N11, ACC_D, ACC_N14, ACC_N6A, ACC_N12A, ACC_N19,
-                       ACC_TT, ACC_N4, ACC_N9A, ACC_N7A, ACC_N15, ACC_TD};
-  LocalAcc<13> l13;
-  for (int i = 0; i < 13; ++i) l13.v[i] = la.v[i];
-  flush_acc(l13, ids, acc, sh);
+  final_flush(la, ids, acc, sh);
 }
 
 // ============================================================================
@@ -933,12 +939,16 @@ __device__ __forceinline__ u128 cnk(u128 n, int k) {
   return r;
 }
 
-__global__ void k_assemble(const Acc128* acc, unsigned long long n_, unsigned long long m_, ConvTables tabs,
-                           unsigned long long* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One thread per graph: graph k reads accumulator row k and writes result k.
+__global__ void k_assemble(const Acc128* acc_all, const unsigned long long* n_arr, const unsigned long long* m_arr,
+                           int num_graphs, ConvTables tabs, unsigned long long* out_all) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_graphs) return;
+  const Acc128* acc = acc_all + (int64_t)k * ACC_COUNT;
+  unsigned long long* out = out_all + (int64_t)k * 2 * 98;
   u128 A[ACC_COUNT];
   for (int i = 0; i < ACC_COUNT; ++i) A[i] = ((u128)acc[i].hi << 64) | acc[i].lo;
-  u128 n = n_, m = m_;
+  u128 n = n_arr[k], m = m_arr[k];
   u128 W = A[ACC_W], T = A[ACC_T], TT = A[ACC_TT], C4 = A[ACC_C4], D = A[ACC_D];
   u128 K4 = A[ACC_K4] / 3, S3 = A[ACC_S3];
   u128 P4 = A[ACC_P4A] - 3 * T;
@@ -1011,6 +1021,23 @@ static unsigned grid_for(int64_t work, int threads, int sms) {
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;
+}
+
+// batch bookkeeping: graph of every rank-space vertex; vertices and edges per graph
+__global__ void k_graph_of_vertex(const int64_t* voff, int num_graphs, const int32_t* rank, int64_t n, int32_t* vg) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+    int lo = 0, hi = num_graphs;          // last k with voff[k] <= u
+    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= u) lo = mid; else hi = mid; }
+    vg[rank[u]] = lo;
+  }
+}
+__global__ void k_graph_sizes(const int64_t* voff, const int64_t* rp, int num_graphs, unsigned long long* n_arr,
+                              unsigned long long* m_arr) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_graphs) return;
+  n_arr[k] = (unsigned long long)(voff[k + 1] - voff[k]);
+  m_arr[k] = (unsigned long long)((rp[voff[k + 1]] - rp[voff[k]]) / 2);
 }
 
 // item lists of pass A/B: vertices by out-degree class
@@ -1098,6 +1125,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   phase();
 
   DevGraph g{n, nnz, o.R, o.C, o.op, o.rev};
+  const int TPB = 256;
   // ---------------- per-element arrays and accumulators
   DevBuf b_T, b_K4e, b_C4e, b_tv, b_C4v, b_K4v, b_acc, b_ctr;
   ESC_TRY(b_T.alloc(sizeof(uint32_t) * (nnz + 1)));
@@ -1106,7 +1134,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_tv.alloc(sizeof(unsigned long long) * (n + 1)));
   ESC_TRY(b_C4v.alloc(sizeof(unsigned long long) * (n + 1)));
   ESC_TRY(b_K4v.alloc(sizeof(unsigned long long) * (n + 1)));
-  ESC_TRY(b_acc.alloc(sizeof(Acc128) * ACC_COUNT));
+  const int G = cfg.num_graphs > 1 ? cfg.num_graphs : 1;
+  ESC_TRY(b_acc.alloc(sizeof(Acc128) * ACC_COUNT * G));
   ESC_TRY(b_ctr.alloc(sizeof(unsigned long long) * 16));
   uint32_t* T = b_T.as<uint32_t>();
   unsigned long long *K4e = b_K4e.as<unsigned long long>(), *C4e = b_C4e.as<unsigned long long>();
@@ -1118,11 +1147,28 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   cudaMemsetAsync(K4e, 0, sizeof(unsigned long long) * (nnz + 1), s);
   cudaMemsetAsync(C4e, 0, sizeof(unsigned long long) * (nnz + 1), s);
   cudaMemsetAsync(C4v, 0, sizeof(unsigned long long) * (n + 1), s);
-  cudaMemsetAsync(acc, 0, sizeof(Acc128) * ACC_COUNT, s);
+  cudaMemsetAsync(acc, 0, sizeof(Acc128) * ACC_COUNT * G, s);
+  DevBuf b_vg, b_narr, b_marr;
+  ESC_TRY(b_narr.alloc(sizeof(unsigned long long) * G));
+  ESC_TRY(b_marr.alloc(sizeof(unsigned long long) * G));
+  AccSet accs{acc, nullptr};
+  if (G > 1) {
+    ESC_TRY(b_vg.alloc(sizeof(int32_t) * (n + 1)));
+    if (n > 0)
+      (k_graph_of_vertex<<<grid_for(n, TPB, sms), TPB, 0, s>>>(cfg.d_vtx_offsets, G, o.rank, n, b_vg.as<int32_t>()),
+       note_launch());
+    (k_graph_sizes<<<(G + 127) / 128, 128, 0, s>>>(cfg.d_vtx_offsets, rp, G, b_narr.as<unsigned long long>(),
+                                                   b_marr.as<unsigned long long>()), note_launch());
+    accs.vg = b_vg.as<int32_t>();
+  } else {
+    unsigned long long nm[2] = {(unsigned long long)n, (unsigned long long)(nnz / 2)};
+    cudaMemcpyAsync(b_narr.p, &nm[0], sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b_marr.p, &nm[1], sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+    ESC_TRY(cudaStreamSynchronize(s));   // nm lives on this stack frame
+  }
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
 
-  const int TPB = 256;
-  if (n > 0) (k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, acc), note_launch());
+  if (n > 0) (k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, accs), note_launch());
 
   // ---------------- item lists for the out-neighbourhood passes
   DevBuf b_small, b_large, b_dims;
@@ -1148,11 +1194,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   size_t smem_a = sizeof(int32_t) * (2 * (size_t)hcap_a) + sizeof(uint32_t) * dmax;
   int grid_sweep = sms * (cfg.cta_per_sm > 0 ? cfg.cta_per_sm : 1);
   if (nsmall > 0)
-    (k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, acc), note_launch());
+    (k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, accs), note_launch());
   if (nlarge > 0) {
     if (smem_a > 48 * 1024) ESC_TRY(cudaFuncSetAttribute(k_tri_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
     (k_tri_large<<<(unsigned)std::min<int64_t>(grid_sweep, nlarge), 512, smem_a, s>>>(
-        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, acc, hcap_a), note_launch());
+        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, accs, hcap_a), note_launch());
   }
   if (n > 0) {
     (k_sym_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv), note_launch());
@@ -1187,7 +1233,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
     if (nitems > 0)
       (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems), 512, smem_b, s>>>(
-          g, b_items.as<int32_t>(), nitems, ctr + 1, T, K4e, acc, cs, hcap, dmax, d_status), note_launch());
+          g, b_items.as<int32_t>(), nitems, ctr + 1, T, K4e, accs, cs, hcap, dmax, d_status), note_launch());
     if (n > 0) {
       (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e), note_launch());
       (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e, K4v, 3), note_launch());
@@ -1210,14 +1256,14 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
 
   // ---------------- 4-cycles (Thm 5)
   if (n > 0) {
-    (k_cycles4<<<grid_sweep, 512, 0, s>>>(g, ctr + 2, ss, C4e, C4v, acc), note_launch());
+    (k_cycles4<<<grid_sweep, 512, 0, s>>>(g, ctr + 2, ss, C4e, C4v, accs), note_launch());
     (k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, C4e), note_launch());
   }
   phase();
 
   // ---------------- closed forms over vertices and edges
   if (n > 0)
-    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, acc), note_launch());
+    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, accs), note_launch());
 
   // ---------------- common-neighbour lists: ids (canonical) and positions (per slot)
   DevBuf b_off, b_offp, b_U, b_P, b_gh;
@@ -1260,7 +1306,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   phase();
 
   // ---------------- pairs: N13, N17 (Thms 11, 12)
-  if (n > 0) (k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, acc), note_launch());
+  if (n > 0) (k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, accs), note_launch());
   phase();
   // ---------------- wheels: N18 (Thm 11)
   {
@@ -1274,7 +1320,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
       while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] > WHEEL_WARP_MAX) hi = mid; else lo = mid + 1; }
       c0 = lo;
       if (c0 > 0)
-        (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s>>>(g, c0, tl3, T, acc), note_launch());
+        (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s>>>(g, c0, tl3, T, accs), note_launch());
       if (c0 < n) {
         std::vector<int64_t> item_off(n - c0 + 1);
         item_off[0] = 0;
@@ -1297,14 +1343,14 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
         size_t smem_w = sizeof(uint32_t) * (size_t)std::max(smem_cap, 1);
         ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
         (k_wheels_cta<<<blocks, 512, smem_w, s>>>(g, c0, b_io.as<int64_t>(), nitems, ctr + 5, tl3, T,
-                                                  b_gs.as<uint32_t>(), gstride, smem_cap, acc), note_launch());
+                                                  b_gs.as<uint32_t>(), gstride, smem_cap, accs), note_launch());
         ESC_TRY(cudaStreamSynchronize(s));
       }
     }
   }
   phase();
   // ---------------- 5-cycles (Thm 13)
-  if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, acc), note_launch());
+  if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, accs), note_launch());
   phase();
 
   // ---------------- assembly
@@ -1312,7 +1358,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   conversion_inverse(3, tabs.a3);
   conversion_inverse(4, tabs.a4);
   conversion_inverse(5, tabs.a5);
-  (k_assemble<<<1, 32, 0, s>>>(acc, (unsigned long long)n, (unsigned long long)(nnz / 2), tabs, d_out), note_launch());
+  (k_assemble<<<(G + 63) / 64, 64, 0, s>>>(acc, b_narr.as<unsigned long long>(), b_marr.as<unsigned long long>(), G,
+                                          tabs, d_out), note_launch());
   phase();
 
   if (pe_out) {

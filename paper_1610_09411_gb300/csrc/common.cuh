@@ -98,6 +98,53 @@ __device__ __forceinline__ void flush_acc(LocalAcc<K>& la, const int (&ids)[K], 
   }
 }
 
+// Accumulator set: one row of ACC_COUNT counters per graph.  vg (graph id of
+// every vertex) is null for a single graph; then every item adds to row 0 and
+// partial sums are flushed once per block at the end.  In a batch, every work
+// item belongs to one graph (no edge joins two graphs), so its partial sums are
+// flushed to that graph's row when the item is done.
+struct AccSet {
+  Acc128* base;
+  const int32_t* vg;
+};
+
+__device__ __forceinline__ Acc128* acc_of(const AccSet& A, int64_t v) {
+  return A.vg ? A.base + (int64_t)A.vg[v] * ACC_COUNT : A.base;
+}
+
+// per-item flush for warp-per-item loops (all 32 lanes present)
+template <int K>
+__device__ __forceinline__ void warp_item_flush(LocalAcc<K>& la, const int (&ids)[K], const AccSet& A, int64_t v) {
+  if (!A.vg) return;
+  Acc128* a = acc_of(A, v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    u128 s = warp_sum_u128(la.v[i]);
+    if ((threadIdx.x & 31) == 0) acc_add(a, ids[i], s);
+    la.v[i] = 0;
+  }
+}
+
+// per-item flush for CTA-per-item loops (all threads of the block present)
+template <int K>
+__device__ __forceinline__ void block_item_flush(LocalAcc<K>& la, const int (&ids)[K], const AccSet& A, int64_t v,
+                                                 u128* sh) {
+  if (!A.vg) return;
+  Acc128* a = acc_of(A, v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    u128 s = block_sum_u128(la.v[i], sh);
+    if (threadIdx.x == 0) acc_add(a, ids[i], s);
+    la.v[i] = 0;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void final_flush(LocalAcc<K>& la, const int (&ids)[K], const AccSet& A, u128* sh) {
+  if (A.vg) return;
+  flush_acc(la, ids, A.base, sh);
+}
+
 __device__ __forceinline__ u128 ch2(unsigned long long x) { return x < 2 ? 0 : (u128)x * (x - 1) / 2; }
 __device__ __forceinline__ u128 ch3(unsigned long long x) {
   if (x < 3) return 0;

@@ -4,6 +4,7 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -185,6 +186,25 @@ int device_sms(int dev) {
 __global__ void k_rebase_rows(const int64_t* rp, int64_t n, int64_t base, int64_t* out) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) out[i] = rp[i] - base;
+}
+
+// batch: local ids of graph k's rows become union ids (add the graph's first
+// vertex); an id outside its own graph is flagged and left in range
+__global__ void k_globalize(const int64_t* voff, int num_graphs, const int64_t* rp, int64_t rows, int32_t* col,
+                            unsigned* status) {
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int lane = threadIdx.x & 31;
+  for (int64_t r = warp; r < rows; r += nwarps) {
+    int lo = 0, hi = num_graphs;
+    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (voff[mid] <= r) lo = mid; else hi = mid; }
+    int64_t base = voff[lo], nk = voff[lo + 1] - base;
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+      int32_t v = col[p];
+      if (v < 0 || v >= nk) { atomicOr(status, 1u); col[p] = (int32_t)r; continue; }   // later rejected
+      col[p] = (int32_t)(base + v);
+    }
+  }
 }
 
 // input slot p (u -> v, original ids) -> value at the rank-space slot
@@ -395,58 +415,101 @@ escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offset
   if (num_graphs == 0) return ESCAPE_OK;
   cudaStream_t s = (cudaStream_t)stream;
   bool dev_ptrs = (flags & ESCAPE_DEVICE_PTRS) != 0;
+  cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = device_sms(dev);
+  // sizes on the host: the vertex offsets and the total entry count
   std::vector<int64_t> voff(num_graphs + 1);
-  cudaError_t e;
-  if (dev_ptrs) {
-    e = cudaMemcpyAsync(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return from_cuda(e);
-  } else {
-    memcpy(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1));
-  }
+  cudaError_t e = cudaSuccess;
+  if (dev_ptrs) e = cudaMemcpyAsync(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, s);
+  else memcpy(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
   if (voff[0] != 0) return ESCAPE_EINVAL;
   for (int k = 0; k < num_graphs; ++k)
     if (voff[k + 1] < voff[k] || voff[k + 1] - voff[k] > 2147483647LL) return ESCAPE_EINVAL;
   int64_t rows = voff[num_graphs];
-  std::vector<int64_t> hrp;
-  const int64_t* rp_host = nullptr;
+  if (rows > 2147483647LL) return ESCAPE_EOVERFLOW;      // the union is one graph of int32 ids
+  int64_t ends[2] = {0, 0};
   if (dev_ptrs) {
-    hrp.resize(rows + 1);
-    e = cudaMemcpyAsync(hrp.data(), row_ptr, sizeof(int64_t) * (rows + 1), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(&ends[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
-    rp_host = hrp.data();
   } else {
-    rp_host = row_ptr;
+    ends[0] = row_ptr[0];
+    ends[1] = row_ptr[rows];
+    for (int64_t r = 0; r < rows; ++r)
+      if (row_ptr[r + 1] < row_ptr[r]) return ESCAPE_EINVAL;
   }
-  if (rp_host[0] != 0) return ESCAPE_EINVAL;
-  std::vector<escape_census> res(num_graphs);
-  std::vector<int64_t> local;
-  for (int k = 0; k < num_graphs; ++k) {
-    int64_t v0 = voff[k], n = voff[k + 1] - v0;
-    int64_t e0 = rp_host[v0], nnz = rp_host[v0 + n] - e0;
-    if (nnz < 0) return ESCAPE_EINVAL;
-    escape_graph* g = nullptr;
-    escape_status st;
-    if (dev_ptrs) {
-      int64_t* d_rp = nullptr;
-      e = cudaMalloc(&d_rp, sizeof(int64_t) * (n + 1));
-      if (e != cudaSuccess) return from_cuda(e);
-      (k_rebase_rows<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(row_ptr + v0, n, e0, d_rp), esc::note_launch());
-      st = escape_load_csr(n, nnz, d_rp, col + e0, flags, stream, &g);
-      cudaFree(d_rp);
-    } else {
-      local.resize(n + 1);
-      for (int64_t i = 0; i <= n; ++i) local[i] = rp_host[v0 + i] - e0;
-      st = escape_load_csr(n, nnz, local.data(), col + e0, flags, stream, &g);
+  if (ends[0] != 0 || ends[1] < 0) return ESCAPE_EINVAL;
+  int64_t nnz = ends[1];
+  if (nnz > 0 && !col) return ESCAPE_EINVAL;
+  // device copies: offsets, rows, entries turned into union ids
+  int64_t *d_voff = nullptr, *d_rp = nullptr;
+  int32_t* d_col = nullptr;
+  unsigned* d_status = nullptr;
+  unsigned long long* d_out = nullptr;
+  e = cudaMalloc(&d_voff, sizeof(int64_t) * (num_graphs + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_rp, sizeof(int64_t) * (rows + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_col, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(escape_census) * num_graphs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_voff, voff.data(), sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (rows + 1), kind, s);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, kind, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
+  escape_status st = from_cuda(e);
+  if (st == ESCAPE_OK && rows > 0) {
+    (k_globalize<<<(unsigned)std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sms * 16), 256, 0, s>>>(
+         d_voff, num_graphs, d_rp, rows, d_col, d_status), esc::note_launch());
+    st = from_cuda(cudaGetLastError());
+  }
+  if (st == ESCAPE_OK && (flags & ESCAPE_NORMALIZE)) {
+    esc::DeviceArena arena;
+    size_t ab = (size_t)(2 * nnz + 16) * 8 * 3 + (size_t)((2 * nnz) / 4096 + 2) * 256 * 8 * 2 + (1 << 22);
+    e = cudaMalloc(&arena.base, ab);
+    if (e == cudaSuccess) {
+      arena.cap = ab;
+      int64_t* nrp = nullptr;
+      int32_t* ncol = nullptr;
+      int64_t nnz2 = 0;
+      e = esc::normalize_csr(rows, nnz, d_rp, d_col, &nrp, &ncol, &nnz2, d_status, arena, s, sms);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(arena.base);
+      if (e == cudaSuccess) { cudaFree(d_rp); cudaFree(d_col); d_rp = nrp; d_col = ncol; nnz = nnz2; }
     }
-    if (st != ESCAPE_OK) return st;
-    st = escape_census5(g, &res[k], stream);
-    escape_free(g);
-    if (st != ESCAPE_OK) return st;
+    st = from_cuda(e);
+  } else if (st == ESCAPE_OK) {
+    st = from_cuda(esc::validate_csr(rows, d_rp, d_col, d_status, s, sms));
   }
-  memcpy(out, res.data(), sizeof(escape_census) * num_graphs);
-  return ESCAPE_OK;
+  if (st == ESCAPE_OK) {
+    unsigned h = 0;
+    e = cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = from_cuda(e);
+    if (st == ESCAPE_OK && h) st = ESCAPE_EINVAL;
+  }
+  if (st == ESCAPE_OK) {
+    esc::CensusConfig cfg;
+    cfg.sms = sms;
+    cfg.cta_per_sm = 2;
+    cfg.d_vtx_offsets = d_voff;
+    cfg.num_graphs = num_graphs;
+    e = esc::run_census(d_rp, d_col, rows, nnz, nullptr, 0, cfg, d_out, d_status, nullptr, nullptr, s);
+    st = from_cuda(e);
+    unsigned h = 0;
+    if (st == ESCAPE_OK) {
+      e = cudaMemcpyAsync(out, d_out, sizeof(escape_census) * num_graphs, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      st = from_cuda(e);
+      if (st == ESCAPE_OK && h) st = ESCAPE_EINTERNAL;
+    }
+  }
+  cudaFree(d_voff); cudaFree(d_rp); cudaFree(d_col); cudaFree(d_status); cudaFree(d_out);
+  return st;
 }
 
 escape_status escape_per_element(escape_graph* g, uint64_t* tri_e, uint64_t* c4_e, uint64_t* k4_e, uint64_t* tri_v,

@@ -78,6 +78,11 @@ struct CensusConfig {
   bool keep_per_element = false;
   cudaEvent_t* phase_events = nullptr;   // optional: records an event after each phase
   int num_phase_events = 0;
+  // batch: the graph is the block-diagonal union of num_graphs graphs whose
+  // vertices are [d_vtx_offsets[k], d_vtx_offsets[k+1]) (device array); d_out
+  // then receives num_graphs results
+  const int64_t* d_vtx_offsets = nullptr;
+  int num_graphs = 1;
 };
 
 size_t census_scratch_bytes(int64_t n, int64_t nnz, int sms, int cta_per_sm);

@@ -34,6 +34,9 @@ WORKLOADS = {
     "chung_lu": "Chung-Lu power law n=262144, exponent 2.1, mean degree 16, max 8192, seed 1 (~2.0M edges)",
     "rmat22": "R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), seed 1 (~64.2M edges)",
     "er500": "Erdos-Renyi G(500, 0.012), seed 0",
+    "batch": "batch of graphs: sizes uniform 20-2000, half G(n,p) p~U(0.01,0.3), half BA m~U{2..6}, seed 2024",
+    "serve": "Poisson stream of Chung-Lu (exponent 2.3, mean degree 16) requests, m log-uniform 1e3-5e6, "
+             "120 GB admission budget",
 }
 # per-kernel algorithmic bytes: (phase, kernel, description, function of the oracle sums)
 ALG_BYTES = {
@@ -208,6 +211,116 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _pack(graphs):
+    import numpy as np
+    voff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    rps, cols, base = [], [], 0
+    for k, g in enumerate(graphs):
+        voff[k + 1] = voff[k] + g.n
+        rps.append(g.row_ptr[:-1] + base)
+        cols.append(g.col)
+        base += g.nnz
+    rp = np.concatenate(rps + [np.array([base])]).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32)
+    return voff, rp, col
+
+
+def run_batch_bench(args):
+    """Batched census: one fused escape_census5_batch call per step over the
+    whole batch (resident on the device) vs one escape_census5 call per graph."""
+    import torch
+    import graphgen as gg
+    torch.cuda.set_device(0)
+    from paper_1610_09411_gb300 import build as pbuild
+    pbuild.build()
+    from paper_1610_09411_gb300 import escape as esc
+    graphs = gg.batch_graphs(args.batch_count, 2024)
+    edges = sum(g.m for g in graphs)
+    voff, rp, col = _pack(graphs)
+    dv, dr, dc = (torch.from_numpy(x).cuda() for x in (voff, rp, col))
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        res = esc.escape_census5_batch(dv, dr, dc)
+    stream = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = esc.escape_census5_batch(dv, dr, dc)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    ms = total / args.steps
+    # one launch sequence per graph (each graph resident on the device)
+    handles = [esc.escape_load_csr(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+               for g in graphs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = [esc.escape_census5(h) for h in handles]
+    torch.cuda.synchronize()
+    ms_single = 1000 * (time.perf_counter() - t0)
+    for h in handles:
+        esc.escape_free(h)
+    same = all(a == b for a, b in zip(res, single))
+    line = {"metric": "batched graphs/s (full census per graph)", "value": len(graphs) / (ms / 1000.0),
+            "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch"], "graphs": len(graphs), "edges": edges},
+            "edges_per_s": edges / (ms / 1000.0),
+            "one_graph_per_launch": {"graphs_per_s": len(graphs) / (ms_single / 1000.0), "ms": ms_single},
+            "speedup_vs_one_graph_per_launch": ms_single / ms, "results_identical": same}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve_bench(args):
+    """Serving: Poisson arrivals at each rate, continuous batching over three
+    streams vs the one-at-a-time path (one worker, batches of one)."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    torch.cuda.set_device(0)
+    from paper_1610_09411_gb300 import build as pbuild
+    pbuild.build()
+    from paper_1610_09411_gb300 import escape as esc  # noqa: F401
+    from paper_1610_09411_gb300.serve import CensusServer, poisson_arrivals, replay
+    rng_seed = 31
+    graphs = []
+    for k in range(args.serve_requests):
+        u = (gg.stream_draw(rng_seed, 9, k) >> 11) / float(1 << 53)
+        m_target = 10 ** (3 + u * (np.log10(5e6) - 3))
+        n = max(64, int(m_target / 8))
+        graphs.append(gg.chung_lu(n, 2.3, 16.0, max(16.0, min(8192.0, n / 4)), gg.stream_draw(rng_seed, 10, k)))
+    edges = sum(g.m for g in graphs)
+    # warm up the library on a small graph
+    g0 = gg.erdos_renyi(100, 0.1, 1)
+    esc.census(g0.row_ptr, g0.col, n=g0.n)
+    out = {"metric": "served census: p50/p99 latency and edges/s", "unit": "ms", "higher_is_better": False,
+           "n_gpus": 1, "dtype": "u128", "data": "synthetic",
+           "config": {"workload": WORKLOADS["serve"], "requests": len(graphs), "edges": edges,
+                      "workers": 3}, "rates": {}}
+    for rate in [float(r) for r in args.serve_rates.split(",")]:
+        arr = poisson_arrivals(rate, len(graphs), 7)
+        row = {}
+        for mode, kw in (("continuous_batching", dict(workers=3)),
+                         ("one_at_a_time", dict(workers=1, max_batch=1))):
+            srv = CensusServer(budget_bytes=120e9, **kw)
+            t0 = time.perf_counter()
+            futs = replay(srv, graphs, arr)
+            for f in futs:
+                f.result()
+            span = time.perf_counter() - t0
+            srv.close()
+            st = srv.latency_stats()
+            st["edges_per_s"] = edges / span
+            st["makespan_s"] = span
+            row[mode] = st
+        out["rates"][str(int(rate))] = row
+    best = out["rates"][max(out["rates"], key=lambda r: float(r))]["continuous_batching"]
+    out["value"] = best["p99_ms"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,11 +329,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chung_lu", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=1000, help="graphs in the batch workload (config: 10000)")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-rates", default="100,1000,10000")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_bench(args)
+    if args.workload == "serve":
+        return run_serve_bench(args)
 
     import numpy as np
     import torch

@@ -64,6 +64,7 @@ class CensusServer:
         self.lock = threading.Condition()
         self.closed = False
         self.device = device
+        self._gpu = run_batch is None
         self._run_batch = run_batch or self._gpu_run_batch
         self._upload = upload or self._gpu_upload
         self.completed: list[Request] = []
@@ -161,7 +162,7 @@ class CensusServer:
                     r.future.set_result(results[i])
 
     def _make_stream(self):
-        if self._run_batch is not self._gpu_run_batch:
+        if not self._gpu:
             return None
         import torch
         torch.cuda.set_device(self.device)

@@ -211,6 +211,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def slowest_rank_ms(total_ms: float, world: int, device: str) -> float:
+    """Max over ranks of the timed region (replicas: the job ends with the slowest)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_value(world: int, m: int, ms_per_step: float) -> float:
+    """Whole-job edges/s: every rank counted its own copy of the graph."""
+    return world * m / (ms_per_step / 1000.0)
+
+
 def _pack(graphs):
     import numpy as np
     voff = np.zeros(len(graphs) + 1, dtype=np.int64)
@@ -392,13 +409,9 @@ def main():
         launches += esc.escape_last_kernel_launches(h)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = slowest_rank_ms(total_ms, world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * g.m / (ms_per_step / 1000.0)
+    value = replica_value(world, g.m, ms_per_step)
 
     # end to end through the public C ABI with pinned host buffers: H2D of the
     # CSR, the census, D2H of the result struct, every step

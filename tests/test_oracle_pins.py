@@ -251,3 +251,19 @@ def test_planted_mistakes_are_caught():
         mut(T)
         c = oracle.induced_from_noninduced(oracle.noninduced_from_sums(T))["c5"]
         assert c != truth, name
+
+
+def test_single_element_definitions_match_full_census():
+    """The sampled-check helpers (single edges / vertices from their
+    definitions) agree with the whole-graph per-element arrays."""
+    g = gg.chung_lu(600, 2.1, 8, 80, 6)
+    pe = oracle.census(g, per_element=True)["per_element"]
+    src = np.repeat(np.arange(g.n), g.degrees())
+    idx = np.arange(0, g.nnz, 5)
+    e = oracle.edge_elements(g, src[idx], g.col[idx])
+    for k in ("T_e", "K4_e", "C4_e"):
+        assert np.array_equal(e[k], pe[k][idx]), k
+    vs = np.arange(0, g.n, 4)
+    v = oracle.vertex_elements(g, vs)
+    for k in ("t_i", "C4_i"):
+        assert np.array_equal(v[k], pe[k][vs]), k

@@ -527,11 +527,37 @@ struct TriLists {
 // j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
 // per-edge triangle lists).
 // ============================================================================
+// Counters of the pair sweep.  NARROW: two 16-bit counters per 32-bit word
+// (used when every degree is below 2^16, so no W(i,j) can reach 2^16); this
+// halves the per-CTA footprint so more of the counters stay in L2.
+template <bool NARROW>
+struct PairCounters {
+  uint32_t* w;
+  __device__ __forceinline__ uint32_t inc(int32_t j) const {
+    if (NARROW) {
+      unsigned sh = (unsigned)(j & 1) << 4;
+      uint32_t old = atomicAdd(&w[j >> 1], 1u << sh);
+      return (old >> sh) & 0xffffu;
+    }
+    return atomicAdd(&w[j], 1u);
+  }
+  __device__ __forceinline__ uint32_t get(int32_t j) const {
+    if (NARROW) return (w[j >> 1] >> ((unsigned)(j & 1) << 4)) & 0xffffu;
+    return w[j];
+  }
+  __device__ __forceinline__ void clear(int32_t j) const {
+    if (NARROW) ((unsigned short*)w)[j] = 0;   // little-endian: half j&1 of word j>>1
+    else w[j] = 0;
+  }
+};
+
+template <bool NARROW>
 __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
                         AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
+  int64_t stride = NARROW ? (ss.n + 1) / 2 : ss.n;
+  PairCounters<NARROW> w{ss.cnt + (int64_t)blockIdx.x * stride};
   int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
   unsigned* nt = ss.ntouched + 2 * blockIdx.x;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -552,7 +578,7 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
       int64_t cb = g.R[c], ce = g.rev[p];       // N(c) below i
       for (int64_t q = cb + lane; q < ce; q += 32) {
         int32_t j = g.C[q];
-        uint32_t old = atomicAdd(&w[j], 1u);
+        uint32_t old = w.inc(j);
         if (old == 0) tl[atomicAdd(nt, 1u)] = j;
         else n13 += (u128)old * (old - 1) / 2;
       }
@@ -576,12 +602,12 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
         for (int64_t s = vb + lane; s < ve; s += 32) {
           int32_t j = tl3.U[s];
           if (j >= i) break;
-          n17 += (u128)(w[j] - 2);
+          n17 += (u128)(w.get(j) - 2);
         }
       }
     }
     __syncthreads();
-    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
+    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w.clear(tl[t]);
     la.v[0] += n13;
     la.v[1] += n17;
     block_item_flush(la, ids, acc, i, sh);
@@ -1306,7 +1332,13 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   phase();
 
   // ---------------- pairs: N13, N17 (Thms 11, 12)
-  if (n > 0) (k_pairs<<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, accs), note_launch());
+  if (n > 0) {
+    // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
+    if (maxdeg < 65536)
+      (k_pairs<true><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, accs), note_launch());
+    else
+      (k_pairs<false><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, accs), note_launch());
+  }
   phase();
   // ---------------- wheels: N18 (Thm 11)
   {

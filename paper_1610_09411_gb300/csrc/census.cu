@@ -627,6 +627,18 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
 // ============================================================================
 static constexpr int WHEEL_WARP_MAX = 1024;     // centres up to this degree: one warp each
 
+// Counter tagged with the u it belongs to: (tag << 16) | count.  An entry whose
+// tag differs counts as zero, so nothing has to be cleared between u's.
+__device__ __forceinline__ uint32_t tagged_inc(uint32_t* p, uint32_t tag) {
+  uint32_t old = *(volatile uint32_t*)p, assumed;
+  do {
+    assumed = old;
+    uint32_t nv = ((assumed >> 16) == tag) ? assumed + 1 : ((tag << 16) | 1u);
+    old = atomicCAS(p, assumed, nv);
+  } while (old != assumed);
+  return ((assumed >> 16) == tag) ? (assumed & 0xffffu) : 0u;
+}
+
 __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ uint32_t scr_all[8][WHEEL_WARP_MAX];
@@ -637,17 +649,18 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uin
   const int ids[1] = {ACC_N18};
   LocalAcc<1> la;
   la.zero();
-  for (int i = lane; i < WHEEL_WARP_MAX; i += 32) scr[i] = 0;
-  __syncwarp();
   for (int64_t c = warp; c < c_end; c += nwarps) {
     int64_t base = g.R[c];
     int d = (int)(g.R[c + 1] - base);
     if (d < 4) continue;
+    for (int i = lane; i < d; i += 32) scr[i] = 0;       // tags of the previous centre
+    __syncwarp();
     u128 n18 = 0;
     for (int pu = 0; pu < d; ++pu) {
       uint32_t lenu = T[base + pu];
       if (lenu < 2) continue;
       const int32_t* Lu = tl3.P + tl3.offp[base + pu];
+      uint32_t tag = (uint32_t)pu + 1;                   // <= 1024: fits the 16-bit tag
       unsigned long long part = 0;
       for (uint32_t a = 0; a < lenu; ++a) {
         int32_t pk = Lu[a];
@@ -657,24 +670,12 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uin
         for (uint32_t t = lane; t < lenk; t += 32) {
           int32_t pv = Lk[t];
           if (pv >= pu) break;
-          part += atomicAdd(&scr[pv], 1u);
+          part += tagged_inc(&scr[pv], tag);
         }
       }
-      __syncwarp();
-      for (uint32_t a = 0; a < lenu; ++a) {
-        int32_t pk = Lu[a];
-        if (pk >= pu) break;
-        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
-        uint32_t lenk = T[base + pk];
-        for (uint32_t t = lane; t < lenk; t += 32) {
-          int32_t pv = Lk[t];
-          if (pv >= pu) break;
-          scr[pv] = 0;
-        }
-      }
-      __syncwarp();
       n18 += part;
     }
+    __syncwarp();
     la.v[0] += n18;
     warp_item_flush(la, ids, acc, c);
   }

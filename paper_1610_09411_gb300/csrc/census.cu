@@ -19,6 +19,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <initializer_list>
 #include <cstdio>
 #include <vector>
 
@@ -1116,15 +1117,62 @@ struct DevBuf {
 
 #define ESC_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return _e; } while (0)
 
+// Side streams for the concurrent phases; events order them after / before
+// the caller's stream.  Destroyed (after the caller's stream has joined them)
+// when the census returns.
+struct StreamSet {
+  cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};
+  int count = 0;
+  ~StreamSet() {
+    for (int i = 0; i < count; ++i) cudaStreamDestroy(st[i]);
+  }
+  // prio[i] != 0: the device's greatest (most urgent) priority, else its least
+  cudaError_t create(int k, const int* urgent) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (int i = 0; i < k; ++i) {
+      cudaError_t e = cudaStreamCreateWithPriority(&st[i], cudaStreamNonBlocking, urgent[i] ? greatest : least);
+      if (e != cudaSuccess) return e;
+      count = i + 1;
+    }
+    return cudaSuccess;
+  }
+  // every stream in `to` waits for the work enqueued on `from` so far
+  cudaError_t fork_from(cudaStream_t from, std::initializer_list<cudaStream_t> to) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (r != cudaSuccess) return r;
+    r = cudaEventRecord(e, from);
+    for (cudaStream_t t : to)
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(t, e, 0);
+    cudaEventDestroy(e);
+    return r;
+  }
+  // `into` waits for everything enqueued on the side streams
+  cudaError_t join_into(cudaStream_t into) {
+    for (int i = 0; i < count; ++i) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (r != cudaSuccess) return r;
+      r = cudaEventRecord(e, st[i]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(into, e, 0);
+      cudaEventDestroy(e);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  }
+};
+
 cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, void* /*scratch*/,
                        size_t /*scratch_bytes*/, const CensusConfig& cfg, unsigned long long* d_out,
                        unsigned* d_status, PerElement* pe_out, Oriented* or_out, cudaStream_t s) {
   const int sms = cfg.sms > 0 ? cfg.sms : 1;
-  int ev = 0;
-  auto phase = [&]() {
-    if (cfg.phase_events && ev < cfg.num_phase_events) cudaEventRecord(cfg.phase_events[ev++], s);
+  // phase k is timed by events 2k (begin) and 2k+1 (end) on the stream that runs it
+  auto mark = [&](int k, int end, cudaStream_t st) {
+    int i = 2 * k + end;
+    if (cfg.phase_events && i < cfg.num_phase_events) cudaEventRecord(cfg.phase_events[i], st);
   };
-  phase();
+  mark(0, 0, s);
   // ---------------- orientation (Sec. 3.2)
   DevBuf arena_buf;
   DeviceArena arena;
@@ -1149,7 +1197,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   o.op = b_op.as<int64_t>();
   o.rev = b_rev.as<int64_t>();
   ESC_TRY(orient(rp, col, n, nnz, o, arena, s, sms));
-  phase();
+  mark(0, 1, s);
 
   DevGraph g{n, nnz, o.R, o.C, o.op, o.rev};
   const int TPB = 256;
@@ -1217,6 +1265,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
 
   // ---------------- pass A: triangles
+  mark(1, 0, s);
   int hcap_a = pow2_at_least(2 * dmax);
   size_t smem_a = sizeof(int32_t) * (2 * (size_t)hcap_a) + sizeof(uint32_t) * dmax;
   int grid_sweep = sms * (cfg.cta_per_sm > 0 ? cfg.cta_per_sm : 1);
@@ -1231,68 +1280,51 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     (k_sym_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv), note_launch());
     (k_vertex_from_edges_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv), note_launch());
   }
-  phase();
+  mark(1, 1, s);
 
-  // ---------------- pass B: cliques and per-triangle sums
-  {
-    // all vertices with d+ >= 2 go through the CTA path (the bit matrix needs it)
-    int64_t nitems = nsmall + nlarge;
-    DevBuf b_items;
-    ESC_TRY(b_items.alloc(sizeof(int32_t) * (nitems + 1)));
-    if (nlarge) cudaMemcpyAsync(b_items.p, b_large.p, sizeof(int32_t) * nlarge, cudaMemcpyDeviceToDevice, s);
-    if (nsmall) cudaMemcpyAsync(b_items.as<int32_t>() + nlarge, b_small.p, sizeof(int32_t) * nsmall, cudaMemcpyDeviceToDevice, s);
-    int W_cap = (dmax + 63) >> 6;
-    int hcap = pow2_at_least(2 * dmax);
-    size_t smem_b = sizeof(uint64_t) * ((size_t)dmax * W_cap + dmax) + sizeof(int32_t) * (2 * (size_t)hcap) +
-                    sizeof(uint32_t) * dmax;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int smem_optin = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem_b + 1024 > (size_t)smem_optin) {
-      return cudaErrorInvalidConfiguration;   // out-degree beyond the shared-memory bit matrix
-    }
-    ESC_TRY(cudaFuncSetAttribute(k_clique_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-    int blocks_b = sms;   // one CTA per SM (large shared memory)
-    unsigned long long dwords = dims[0] > 0 ? dims[0] : 1;
-    DevBuf b_D;
-    ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
-    CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
-    if (nitems > 0)
-      (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems), 512, smem_b, s>>>(
-          g, b_items.as<int32_t>(), nitems, ctr + 1, T, K4e, accs, cs, hcap, dmax, d_status), note_launch());
-    if (n > 0) {
-      (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e), note_launch());
-      (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, K4e, K4v, 3), note_launch());
-    }
-    ESC_TRY(cudaStreamSynchronize(s));   // b_items / b_D go out of scope
-  }
-  phase();
+  // ---------------- everything the concurrent phases need is sized and
+  // allocated here, so no branch below waits on the host
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // pass B inputs
+  int64_t nitems_b = nsmall + nlarge;
+  DevBuf b_items, b_D;
+  ESC_TRY(b_items.alloc(sizeof(int32_t) * (nitems_b + 1)));
+  if (nlarge) cudaMemcpyAsync(b_items.p, b_large.p, sizeof(int32_t) * nlarge, cudaMemcpyDeviceToDevice, s);
+  if (nsmall) cudaMemcpyAsync(b_items.as<int32_t>() + nlarge, b_small.p, sizeof(int32_t) * nsmall, cudaMemcpyDeviceToDevice, s);
+  int W_cap = (dmax + 63) >> 6;
+  int hcap_b = pow2_at_least(2 * dmax);
+  size_t smem_b = sizeof(uint64_t) * ((size_t)dmax * W_cap + dmax) + sizeof(int32_t) * (2 * (size_t)hcap_b) +
+                  sizeof(uint32_t) * dmax;
+  if (smem_b + 1024 > (size_t)smem_optin) return cudaErrorInvalidConfiguration;   // d+ beyond the bit matrix
+  ESC_TRY(cudaFuncSetAttribute(k_clique_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  const int blocks_b = sms;   // one CTA per SM (large shared memory)
+  unsigned long long dwords = dims[0] > 0 ? dims[0] : 1;
+  ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
+  CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
 
-  // ---------------- sweep scratch
-  DevBuf b_cnt, b_tl, b_cnt2, b_tl2, b_nt;
-  ESC_TRY(b_cnt.alloc(sizeof(uint32_t) * (size_t)n * grid_sweep + 16));
-  ESC_TRY(b_tl.alloc(sizeof(int32_t) * (size_t)n * grid_sweep + 16));
-  ESC_TRY(b_cnt2.alloc(sizeof(uint32_t) * (size_t)n * grid_sweep + 16));
-  ESC_TRY(b_tl2.alloc(sizeof(int32_t) * (size_t)n * grid_sweep + 16));
-  ESC_TRY(b_nt.alloc(sizeof(unsigned) * 2 * grid_sweep));
-  cudaMemsetAsync(b_cnt.p, 0, sizeof(uint32_t) * (size_t)n * grid_sweep + 16, s);
-  cudaMemsetAsync(b_cnt2.p, 0, sizeof(uint32_t) * (size_t)n * grid_sweep + 16, s);
-  SweepScratch ss{b_cnt.as<uint32_t>(), b_tl.as<int32_t>(), b_cnt2.as<uint32_t>(), b_tl2.as<int32_t>(),
-                  b_nt.as<unsigned>(), n};
+  // sweep scratch: one set per concurrent sweep (4-cycles, pairs, 5-cycles x2)
+  DevBuf b_cntA, b_tlA, b_cntB, b_tlB, b_cntC, b_tlC, b_cntD, b_tlD, b_ntA, b_ntB, b_ntC;
+  size_t sw = sizeof(uint32_t) * (size_t)n * grid_sweep + 16;
+  ESC_TRY(b_cntA.alloc(sw)); ESC_TRY(b_tlA.alloc(sw));
+  ESC_TRY(b_cntB.alloc(sw)); ESC_TRY(b_tlB.alloc(sw));
+  ESC_TRY(b_cntC.alloc(sw)); ESC_TRY(b_tlC.alloc(sw));
+  ESC_TRY(b_cntD.alloc(sw)); ESC_TRY(b_tlD.alloc(sw));
+  ESC_TRY(b_ntA.alloc(sizeof(unsigned) * 2 * grid_sweep));
+  ESC_TRY(b_ntB.alloc(sizeof(unsigned) * 2 * grid_sweep));
+  ESC_TRY(b_ntC.alloc(sizeof(unsigned) * 2 * grid_sweep));
+  cudaMemsetAsync(b_cntA.p, 0, sw, s);
+  cudaMemsetAsync(b_cntB.p, 0, sw, s);
+  cudaMemsetAsync(b_cntC.p, 0, sw, s);
+  cudaMemsetAsync(b_cntD.p, 0, sw, s);
+  SweepScratch ssA{b_cntA.as<uint32_t>(), b_tlA.as<int32_t>(), nullptr, nullptr, b_ntA.as<unsigned>(), n};
+  SweepScratch ssB{b_cntB.as<uint32_t>(), b_tlB.as<int32_t>(), nullptr, nullptr, b_ntB.as<unsigned>(), n};
+  SweepScratch ssC{b_cntC.as<uint32_t>(), b_tlC.as<int32_t>(), b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(),
+                   b_ntC.as<unsigned>(), n};
 
-  // ---------------- 4-cycles (Thm 5)
-  if (n > 0) {
-    (k_cycles4<<<grid_sweep, 512, 0, s>>>(g, ctr + 2, ss, C4e, C4v, accs), note_launch());
-    (k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, C4e), note_launch());
-  }
-  phase();
-
-  // ---------------- closed forms over vertices and edges
-  if (n > 0)
-    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, accs), note_launch());
-
-  // ---------------- common-neighbour lists: ids (canonical) and positions (per slot)
+  // common-neighbour list offsets and sizes
   DevBuf b_off, b_offp, b_U, b_P, b_gh;
   ESC_TRY(b_off.alloc(sizeof(int64_t) * (nnz + 2)));
   ESC_TRY(b_offp.alloc(sizeof(int64_t) * (nnz + 2)));
@@ -1303,97 +1335,114 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (n > 0) (k_all_counts<<<grid_for(nnz, TPB, sms), TPB, 0, s>>>(T, nnz, offp), note_launch());
   ESC_TRY(exclusive_scan_i64(offp, offp, nnz, true, arena, s));
   int64_t ulen = 0, plen = 0;
+  std::vector<int64_t> hR(n + 1, 0);
   cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&plen, offp + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (n > 0) cudaMemcpyAsync(hR.data(), o.R, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
   if (n > 0) (k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off), note_launch());
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
-  int64_t maxdeg = 0;
-  {
-    int64_t last[2] = {0, 0};
-    if (n > 0) {
-      cudaMemcpyAsync(last, o.R + n - 1, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s);
-      ESC_TRY(cudaStreamSynchronize(s));
-    }
-    maxdeg = last[1] - last[0];                  // the highest rank has the largest degree
-  }
+  int64_t maxdeg = n > 0 ? hR[n] - hR[n - 1] : 0;   // the highest rank has the largest degree
   const int hcap_l = 8192;
   int64_t ghash_cap = pow2_at_least((int)std::max<int64_t>(2 * maxdeg, 2));
   if (2 * maxdeg <= hcap_l) ghash_cap = 2;
   ESC_TRY(b_gh.alloc(sizeof(int32_t) * 2 * (size_t)ghash_cap * grid_sweep + 16));
-  {
-    size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
-    ESC_TRY(cudaFuncSetAttribute(k_tri_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
-    if (n > 0)
-      (k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, offp, T, b_U.as<int32_t>(), b_P.as<int32_t>(),
-                                                   b_gh.as<int32_t>(), ghash_cap, hcap_l, d_status), note_launch());
-  }
+  size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
+  ESC_TRY(cudaFuncSetAttribute(k_tri_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
   TriLists tl3{off, b_U.as<int32_t>(), offp, b_P.as<int32_t>()};
-  phase();
 
-  // ---------------- pairs: N13, N17 (Thms 11, 12)
-  if (n > 0) {
-    // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
-    if (maxdeg < 65536)
-      (k_pairs<true><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, accs), note_launch());
-    else
-      (k_pairs<false><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ss, tl3, T, accs), note_launch());
-  }
-  phase();
-  // ---------------- wheels: N18 (Thm 11)
+  // wheel work items: ranks are in degree order, so the large centres are a suffix
+  int64_t c0 = n;
   {
-    // centres by degree: ranks are in degree order, so the large centres are a suffix
-    int64_t c0 = n;
-    if (n > 0) {
-      std::vector<int64_t> hR(n + 1);
-      cudaMemcpyAsync(hR.data(), o.R, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s);
-      ESC_TRY(cudaStreamSynchronize(s));
-      int64_t lo = 0, hi = n;                    // first rank with degree > WHEEL_WARP_MAX
-      while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] > WHEEL_WARP_MAX) hi = mid; else lo = mid + 1; }
-      c0 = lo;
-      if (c0 > 0)
-        (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s>>>(g, c0, tl3, T, accs), note_launch());
-      if (c0 < n) {
-        std::vector<int64_t> item_off(n - c0 + 1);
-        item_off[0] = 0;
-        for (int64_t c = c0; c < n; ++c)
-          item_off[c - c0 + 1] = item_off[c - c0] + (hR[c + 1] - hR[c] + WHEEL_CHUNK - 1) / WHEEL_CHUNK;
-        int64_t nitems = item_off[n - c0];
-        DevBuf b_io, b_gs;
-        ESC_TRY(b_io.alloc(sizeof(int64_t) * (n - c0 + 1)));
-        cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        int smem_optin = 0;
-        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        int smem_cap = std::max(0, (smem_optin - 4096) / 4);
-        smem_cap = std::min<int64_t>(smem_cap, maxdeg);
-        int blocks = sms;
-        int64_t gstride = maxdeg > smem_cap ? maxdeg : 1;
-        ESC_TRY(b_gs.alloc(sizeof(uint32_t) * (size_t)gstride * blocks + 16));
-        cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * blocks + 16, s);
-        size_t smem_w = sizeof(uint32_t) * (size_t)std::max(smem_cap, 1);
-        ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
-        (k_wheels_cta<<<blocks, 512, smem_w, s>>>(g, c0, b_io.as<int64_t>(), nitems, ctr + 5, tl3, T,
-                                                  b_gs.as<uint32_t>(), gstride, smem_cap, accs), note_launch());
-        ESC_TRY(cudaStreamSynchronize(s));
-      }
-    }
+    int64_t lo = 0, hi = n;                    // first rank with degree > WHEEL_WARP_MAX
+    while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] > WHEEL_WARP_MAX) hi = mid; else lo = mid + 1; }
+    c0 = lo;
   }
-  phase();
-  // ---------------- 5-cycles (Thm 13)
-  if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s>>>(g, ctr + 6, ss, accs), note_launch());
-  phase();
+  DevBuf b_io, b_gs;
+  int64_t nitems_w = 0;
+  int smem_cap = std::max(0, (smem_optin - 4096) / 4);
+  smem_cap = (int)std::min<int64_t>(smem_cap, maxdeg);
+  int64_t gstride = maxdeg > smem_cap ? maxdeg : 1;
+  size_t smem_w = sizeof(uint32_t) * (size_t)std::max(smem_cap, 1);
+  std::vector<int64_t> item_off(n - c0 + 1, 0);
+  if (c0 < n) {
+    for (int64_t c = c0; c < n; ++c)
+      item_off[c - c0 + 1] = item_off[c - c0] + (hR[c + 1] - hR[c] + WHEEL_CHUNK - 1) / WHEEL_CHUNK;
+    nitems_w = item_off[n - c0];
+    ESC_TRY(b_io.alloc(sizeof(int64_t) * (n - c0 + 1)));
+    cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
+    ESC_TRY(b_gs.alloc(sizeof(uint32_t) * (size_t)gstride * sms + 16));
+    cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * sms + 16, s);
+    ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
+  }
 
-  // ---------------- assembly
+  // ---------------- concurrent phases on forked streams
+  // The common-neighbour lists come first (short when alone); then
+  //   s3 (most urgent): wheels      s : pairs
+  //   s1, s2, s4 (least urgent): cliques, 4-cycles, 5-cycles; s joins all.
+  mark(4, 0, s);
+  if (n > 0)
+    (k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, offp, T, b_U.as<int32_t>(), b_P.as<int32_t>(),
+                                                 b_gh.as<int32_t>(), ghash_cap, hcap_l, d_status), note_launch());
+  mark(4, 1, s);
+  StreamSet ss_all;
+  const int urgent[4] = {0, 0, 1, 0};
+  ESC_TRY(ss_all.create(4, urgent));
+  cudaStream_t s1 = ss_all.st[0], s2 = ss_all.st[1], s3 = ss_all.st[2], s4 = ss_all.st[3];
+  ESC_TRY(ss_all.fork_from(s, {s1, s2, s3, s4}));
+
+  // wheels (Thm 11): the longest phase, started first
+  mark(6, 0, s3);
+  if (c0 < n)
+    (k_wheels_cta<<<sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
+                                            b_gs.as<uint32_t>(), gstride, smem_cap, accs), note_launch());
+  if (c0 > 0)
+    (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s3>>>(g, c0, tl3, T, accs), note_launch());
+  mark(6, 1, s3);
+  // pairs (Thms 11, 12); 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
+  mark(5, 0, s);
+  if (n > 0) {
+    if (maxdeg < 65536)
+      (k_pairs<true><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ssB, tl3, T, accs), note_launch());
+    else
+      (k_pairs<false><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ssB, tl3, T, accs), note_launch());
+  }
+  mark(5, 1, s);
+  // cliques and per-triangle sums (Thms 6, 7, 10, 14)
+  mark(2, 0, s1);
+  if (nitems_b > 0)
+    (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), 512, smem_b, s1>>>(
+        g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, dmax, d_status), note_launch());
+  if (n > 0) {
+    (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e), note_launch());
+    (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e, K4v, 3), note_launch());
+  }
+  mark(2, 1, s1);
+  // 4-cycles (Thm 5)
+  mark(3, 0, s2);
+  if (n > 0) {
+    (k_cycles4<<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, ssA, C4e, C4v, accs), note_launch());
+    (k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s2>>>(g, C4e), note_launch());
+  }
+  mark(3, 1, s2);
+  // 5-cycles (Thm 13)
+  mark(7, 0, s4);
+  if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, ssC, accs), note_launch());
+  mark(7, 1, s4);
+  ESC_TRY(ss_all.join_into(s));
+
+  // ---------------- closed forms over vertices and edges, then assembly
+  mark(8, 0, s);
+  if (n > 0)
+    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, accs), note_launch());
   ConvTables tabs;
   conversion_inverse(3, tabs.a3);
   conversion_inverse(4, tabs.a4);
   conversion_inverse(5, tabs.a5);
   (k_assemble<<<(G + 63) / 64, 64, 0, s>>>(acc, b_narr.as<unsigned long long>(), b_marr.as<unsigned long long>(), G,
                                           tabs, d_out), note_launch());
-  phase();
+  mark(8, 1, s);
 
   if (pe_out) {
     // hand the per-element arrays over to the caller (ownership moves)

@@ -248,8 +248,8 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
   if (e != cudaSuccess) { cudaFree(d_out); return from_cuda(e); }
   cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
-  cudaEvent_t evs[10];
-  int nev = phase_ms ? 10 : 0;
+  cudaEvent_t evs[18];
+  int nev = phase_ms ? 18 : 0;
   for (int i = 0; i < nev; ++i) cudaEventCreate(&evs[i]);
   esc::CensusConfig cfg;
   cfg.sms = g->sms;
@@ -272,9 +272,9 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   }
   if (nev) {
     int phases = 0;
-    for (int i = 0; i + 1 < nev; ++i) {
+    for (int i = 0; 2 * i + 1 < nev; ++i) {       // phase i: events 2i .. 2i+1
       float ms = 0;
-      if (cudaEventElapsedTime(&ms, evs[i], evs[i + 1]) == cudaSuccess) { phase_ms[i] = ms; phases = i + 1; }
+      if (cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]) == cudaSuccess) { phase_ms[i] = ms; phases = i + 1; }
     }
     cudaGetLastError();
     *nphase = phases;

@@ -553,8 +553,8 @@ struct PairCounters {
 };
 
 template <bool NARROW>
-__global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, TriLists tl3, const uint32_t* T,
-                        AccSet acc) {
+__global__ void k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
+                        TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   int64_t stride = NARROW ? (ss.n + 1) / 2 : ss.n;
@@ -566,9 +566,9 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, SweepScratch ss, T
   LocalAcc<2> la;
   la.zero();
   while (true) {
-    int64_t it = next_item(qctr, g.n, &sh_item);
+    int64_t it = next_item(qctr, item_hi - item_lo, &sh_item);
     if (it < 0) break;
-    int64_t i = g.n - 1 - it;
+    int64_t i = g.n - 1 - (item_lo + it);
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
     if (e0 - b0 < 2) continue;
     u128 n13 = 0, n17 = 0;
@@ -650,7 +650,8 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uin
   const int ids[1] = {ACC_N18};
   LocalAcc<1> la;
   la.zero();
-  for (int64_t c = warp; c < c_end; c += nwarps) {
+  for (int64_t k = warp; k < c_end; k += nwarps) {
+    int64_t c = c_end - 1 - k;                          // largest (most work) first
     int64_t base = g.R[c];
     int d = (int)(g.R[c + 1] - base);
     if (d < 4) continue;
@@ -1361,7 +1362,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   }
   DevBuf b_io, b_gs;
   int64_t nitems_w = 0;
-  int smem_cap = std::max(0, (smem_optin - 4096) / 4);
+  // counters in shared memory up to half the opt-in size: two CTAs per SM
+  int smem_cap = std::max(0, (smem_optin / 2 - 4096) / 4);
   smem_cap = (int)std::min<int64_t>(smem_cap, maxdeg);
   int64_t gstride = maxdeg > smem_cap ? maxdeg : 1;
   size_t smem_w = sizeof(uint32_t) * (size_t)std::max(smem_cap, 1);
@@ -1372,8 +1374,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     nitems_w = item_off[n - c0];
     ESC_TRY(b_io.alloc(sizeof(int64_t) * (n - c0 + 1)));
     cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
-    ESC_TRY(b_gs.alloc(sizeof(uint32_t) * (size_t)gstride * sms + 16));
-    cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * sms + 16, s);
+    ESC_TRY(b_gs.alloc(sizeof(uint32_t) * (size_t)gstride * 2 * sms + 16));
+    cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * 2 * sms + 16, s);
     ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
   }
 
@@ -1387,15 +1389,18 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
                                                  b_gh.as<int32_t>(), ghash_cap, hcap_l, d_status), note_launch());
   mark(4, 1, s);
   StreamSet ss_all;
-  const int urgent[4] = {0, 0, 1, 0};
-  ESC_TRY(ss_all.create(4, urgent));
-  cudaStream_t s1 = ss_all.st[0], s2 = ss_all.st[1], s3 = ss_all.st[2], s4 = ss_all.st[3];
-  ESC_TRY(ss_all.fork_from(s, {s1, s2, s3, s4}));
+  cudaStream_t s1 = s, s2 = s, s3 = s, s4 = s;
+  if (!cfg.serial_phases) {
+    const int urgent[4] = {0, 0, 1, 0};
+    ESC_TRY(ss_all.create(4, urgent));
+    s1 = ss_all.st[0]; s2 = ss_all.st[1]; s3 = ss_all.st[2]; s4 = ss_all.st[3];
+    ESC_TRY(ss_all.fork_from(s, {s1, s2, s3, s4}));
+  }
 
   // wheels (Thm 11): the longest phase, started first
   mark(6, 0, s3);
   if (c0 < n)
-    (k_wheels_cta<<<sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
+    (k_wheels_cta<<<2 * sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
                                             b_gs.as<uint32_t>(), gstride, smem_cap, accs), note_launch());
   if (c0 > 0)
     (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s3>>>(g, c0, tl3, T, accs), note_launch());
@@ -1403,10 +1408,13 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // pairs (Thms 11, 12); 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
   mark(5, 0, s);
   if (n > 0) {
+    // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can);
+    // whole warps only: the kernel's reductions shuffle across full warps
+    int pthreads = std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
     if (maxdeg < 65536)
-      (k_pairs<true><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ssB, tl3, T, accs), note_launch());
+      (k_pairs<true><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs), note_launch());
     else
-      (k_pairs<false><<<grid_sweep, 512, 0, s>>>(g, ctr + 4, ssB, tl3, T, accs), note_launch());
+      (k_pairs<false><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs), note_launch());
   }
   mark(5, 1, s);
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)

@@ -15,7 +15,7 @@ struct escape_graph {
   int64_t* d_rp = nullptr;     // input CSR, original ids
   int32_t* d_col = nullptr;
   int device = 0, sms = 1;
-  int keep_pe = 0, cta_per_sm = 2;
+  int keep_pe = 0, cta_per_sm = 2, serial = 0;
   bool has_pe = false;
   esc::PerElement pe;
   esc::Oriented ori;
@@ -255,6 +255,7 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   cfg.sms = g->sms;
   cfg.cta_per_sm = g->cta_per_sm;
   cfg.keep_per_element = keep;
+  cfg.serial_phases = g->serial != 0;
   cfg.phase_events = nev ? evs : nullptr;
   cfg.num_phase_events = nev;
   e = esc::run_census(d_rp, d_col, n, nnz, nullptr, 0, cfg, d_out, d_status, keep ? pe : nullptr,
@@ -389,10 +390,11 @@ escape_status escape_graph_info(const escape_graph* g, int64_t* n, int64_t* m) {
   return ESCAPE_OK;
 }
 
-escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_per_sm) {
+escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_per_sm, int serial_phases) {
   if (!g || cta_per_sm < 0 || cta_per_sm > 8) return ESCAPE_EINVAL;
   g->keep_pe = keep_per_element ? 1 : 0;
   g->cta_per_sm = cta_per_sm ? cta_per_sm : 2;
+  g->serial = serial_phases ? 1 : 0;
   return ESCAPE_OK;
 }
 

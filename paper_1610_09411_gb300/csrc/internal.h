@@ -76,6 +76,7 @@ struct CensusConfig {
   int sms = 0;                    // SM count of the device
   int cta_per_sm = 2;             // persistent CTAs per SM for the sweep kernels
   bool keep_per_element = false;
+  bool serial_phases = false;     // run every phase on the caller's stream, one after another
   cudaEvent_t* phase_events = nullptr;   // optional: records an event after each phase
   int num_phase_events = 0;
   // batch: the graph is the block-diagonal union of num_graphs graphs whose

@@ -63,7 +63,7 @@ def _load():
     lib.escape_per_element.restype = c_int
     lib.escape_per_element.argtypes = [P, P, P, P, P, P, P, P]
     lib.escape_set_options.restype = c_int
-    lib.escape_set_options.argtypes = [P, c_int, c_int]
+    lib.escape_set_options.argtypes = [P, c_int, c_int, c_int]
     lib.escape_last_phase_ms.restype = c_int
     lib.escape_last_phase_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), c_int]
     lib.escape_last_kernel_launches.restype = ctypes.c_longlong
@@ -145,8 +145,9 @@ def escape_graph_info(h):
     return n.value, m.value
 
 
-def escape_set_options(h, keep_per_element: bool = False, cta_per_sm: int = 0):
-    _check(LIB.escape_set_options(h, int(bool(keep_per_element)), int(cta_per_sm)), "escape_set_options")
+def escape_set_options(h, keep_per_element: bool = False, cta_per_sm: int = 0, serial_phases: bool = False):
+    _check(LIB.escape_set_options(h, int(bool(keep_per_element)), int(cta_per_sm), int(bool(serial_phases))),
+           "escape_set_options")
 
 
 def escape_census5(h, stream=None) -> dict:

@@ -113,6 +113,24 @@ def test_chung_lu_workload():
     assert_same_census(got, want)
 
 
+def test_serial_and_concurrent_phases_agree():
+    from paper_1610_09411_gb300 import escape as esc
+    g = gg.chung_lu(20000, 2.1, 10, 2000, 8)
+    h = esc.escape_load_csr(g.n, g.row_ptr, g.col)
+    try:
+        esc.escape_set_options(h, True, 0, True)
+        a = esc.escape_census5(h)
+        pa = esc.escape_per_element(h)
+        esc.escape_set_options(h, True, 3, False)
+        b = esc.escape_census5(h)
+        pb = esc.escape_per_element(h)
+    finally:
+        esc.escape_free(h)
+    assert_same_census(a, b)
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+
+
 def test_device_and_host_pointers_agree():
     g = gg.chung_lu(5000, 2.1, 8, 500, 7)
     assert_same_census(gpu_census(g), gpu_census(g, device=True))

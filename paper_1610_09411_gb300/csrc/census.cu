@@ -9,10 +9,11 @@
 //   Thm 7 triangles T(e), t(i) ................ k_tri_small / k_tri_large (pass A)
 //   Thm 6/7 4-cliques K4(e), K4(t); Thm 10 N10,
 //     N16, N20; Thm 14 5-cliques; Thm 13's
-//     directed tailed triangles ................ k_clique_small / k_clique_large (pass B)
+//     directed tailed triangles ................ k_clique_large (pass B)
 //   Thm 5 4-cycles C4(e), C4(i) ................ k_cycles4
+//   Thm 12 common-neighbour lists of edges ..... k_tri_lists
 //   Thm 11/12 N13, N17 (pairs and diamonds) .... k_pairs
-//   Thm 11 N18 (wheels) ........................ k_wheels
+//   Thm 11 N18 (wheels) ........................ k_wheels_warp / k_wheels_cta
 //   Thm 13 5-cycles ............................ k_cycles5
 //   Thm 3 + App. B assembly .................... k_assemble
 #include "common.cuh"
@@ -466,7 +467,7 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       int64_t kb = g.R[k], ke = g.rev[p];       // N(k) below i
       for (int64_t q = kb + lane; q < ke; q += 32) {
         int32_t j = g.C[q];
-        if (atomicAdd(&w[j], 1u) == 0) tl[atomicAdd(nt, 1u)] = j;
+        warp_append(tl, nt, atomicAdd(&w[j], 1u) == 0, j);
       }
     }
     __syncthreads();
@@ -503,14 +504,7 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
   if (threadIdx.x == 0 && !acc.vg) acc_add(acc.base, ACC_C4, c4sum);
 }
 
-// ============================================================================
-// Thm 11/12: N13 = sum_{j<i} C(W(i,j), 3) and
-// N17 = sum_{j<i} (W(i,j) - 2) cc(i,j), cc = edges inside N(i) cap N(j).
-// W(i,.) from every wedge i - c - j (c in N(i), j in N(c), j < i); the cc
-// term is gathered per diamond: for each triangle {i, x, y} (x < y) and each
-// j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
-// per-edge triangle lists).
-// ============================================================================
+// Per-edge common-neighbour lists (built by the triangle-list pass).
 struct TriLists {
   const int64_t* off;    // per slot: start of the edge's id list (both slots of an edge share it)
   const int32_t* U;      // sorted common-neighbour ids
@@ -580,8 +574,8 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, i
       for (int64_t q = cb + lane; q < ce; q += 32) {
         int32_t j = g.C[q];
         uint32_t old = w.inc(j);
-        if (old == 0) tl[atomicAdd(nt, 1u)] = j;
-        else n13 += (u128)old * (old - 1) / 2;
+        n13 += (u128)old * (old - 1) / 2;       // zero for old = 0 and 1
+        warp_append(tl, nt, old == 0, j);
       }
     }
     __syncthreads();
@@ -787,8 +781,7 @@ __global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       int64_t cb = (p < o) ? g.R[c] : g.op[c], ce = g.R[c + 1];
       for (int64_t q = cb + lane; q < ce; q += 32) {
         int32_t j = g.C[q];
-        if (j == i) continue;
-        if (atomicAdd(&wp[j], 1u) == 0) tl[atomicAdd(&nt[0], 1u)] = j;
+        warp_append(tl, &nt[0], j != i && atomicAdd(&wp[j], 1u) == 0, j);
       }
     }
     // P2(i, .)
@@ -796,8 +789,7 @@ __global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       int32_t a = g.C[p];
       for (int64_t q = g.op[a] + lane; q < g.R[a + 1]; q += 32) {
         int32_t b = g.C[q];
-        if (b == i) continue;
-        if (atomicAdd(&p2[b], 1u) == 0) tl2[atomicAdd(&nt[1], 1u)] = b;
+        warp_append(tl2, &nt[1], b != i && atomicAdd(&p2[b], 1u) == 0, b);
       }
     }
     __syncthreads();

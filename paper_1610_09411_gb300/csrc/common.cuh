@@ -184,6 +184,22 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t lo,
   return lo;
 }
 
+// ---------------------------------------------------------------- shared lists
+// Append j to a block-shared list where `take` holds, with one atomic per warp
+// instead of one per entry: the lanes executing together vote, the lowest
+// voter reserves room for all of them and each voter writes its own slot.
+// The order of entries inside the list is unspecified.
+__device__ __forceinline__ void warp_append(int32_t* list, unsigned* n, bool take, int32_t j) {
+  unsigned am = __activemask();
+  unsigned b = __ballot_sync(am, take);
+  if (!b) return;
+  int lane = threadIdx.x & 31, leader = __ffs(b) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(n, (unsigned)__popc(b));
+  base = __shfl_sync(am, base, leader);
+  if (take) list[base + __popc(b & ((1u << lane) - 1u))] = j;
+}
+
 // ---------------------------------------------------------------- status word
 // Device-side error flags (no traps): kernels record the first problem they
 // meet here and skip the offending access; the host turns a non-zero word

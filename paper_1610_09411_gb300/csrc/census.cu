@@ -546,8 +546,10 @@ struct PairCounters {
   }
 };
 
+static constexpr int PAIR_ILP = 4;        // independent accesses in flight per lane
+
 template <bool NARROW>
-__global__ void k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
+__global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
                         TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
@@ -568,36 +570,75 @@ __global__ void k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, i
     u128 n13 = 0, n17 = 0;
     if (threadIdx.x == 0) *nt = 0;
     __syncthreads();
-    for (int64_t p = b0 + wid; p < e0; p += nw) {
-      int32_t c = g.C[p];
-      int64_t cb = g.R[c], ce = g.rev[p];       // N(c) below i
-      for (int64_t q = cb + lane; q < ce; q += 32) {
-        int32_t j = g.C[q];
-        uint32_t old = w.inc(j);
-        n13 += (u128)old * (old - 1) / 2;       // zero for old = 0 and 1
-        warp_append(tl, nt, old == 0, j);
+    // The warp's lists are fetched 32 at a time (lane k holds the k-th), and
+    // each lane keeps PAIR_ILP independent loads and counter operations in
+    // flight: the sweep is bound by the latency of scattered accesses.
+    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
+      int64_t p = pbase + (int64_t)lane * nw;
+      int64_t cb_l = 0, ce_l = 0;
+      if (p < e0) {
+        int32_t c = g.C[p];
+        cb_l = g.R[c];
+        ce_l = g.rev[p];                        // N(c) below i ends at the slot of i
+      }
+      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
+      for (int k = 0; k < kmax; ++k) {
+        int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
+        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
+          int32_t jj[PAIR_ILP];
+          uint32_t oo[PAIR_ILP];
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : -1;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? w.inc(jj[u]) : 1u;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) {
+            n13 += (u128)oo[u] * (oo[u] - 1) / 2;   // zero for old = 0 and 1
+            warp_append(tl, nt, oo[u] == 0, jj[u]);
+          }
+        }
       }
     }
     __syncthreads();
     unsigned ntc = *nt;
-    // diamonds with tip i
+    // diamonds with tip i: for each x in N(i) the triangles {i, x, y} with y
+    // above x (a suffix of the position list of slot (x -> i)); their
+    // common-neighbour lists are sorted, so the j below i are a prefix
     for (int64_t p = b0 + wid; p < e0; p += nw) {
       if (T[p] == 0) continue;
       int32_t x = g.C[p];
       int64_t xb = g.R[x];
       int32_t xo = (int32_t)(g.op[x] - xb);     // positions >= xo in row x are above x
       int64_t rp_ = g.rev[p];                   // slot (x -> i)
-      const int32_t* ys = tl3.P + tl3.offp[rp_];
-      uint32_t ny = T[rp_];
-      for (uint32_t r = 0; r < ny; ++r) {
-        int32_t py = ys[r];
-        if (py < xo) continue;
-        int64_t sxy = xb + py;
-        int64_t vb = tl3.off[sxy], ve = vb + T[sxy];
-        for (int64_t s = vb + lane; s < ve; s += 32) {
-          int32_t j = tl3.U[s];
-          if (j >= i) break;
-          n17 += (u128)(w.get(j) - 2);
+      int64_t yb = tl3.offp[rp_];
+      int64_t ye = yb + T[rp_];
+      for (int64_t rb = lower_bound_i32(tl3.P, yb, ye, xo); rb < ye; rb += 32) {
+        int64_t r = rb + lane;
+        int64_t vb_l = 0;
+        uint32_t len_l = 0;
+        if (r < ye) {
+          int64_t sxy = xb + tl3.P[r];          // slot (x -> y)
+          vb_l = tl3.off[sxy];
+          len_l = T[sxy];
+        }
+        int kmax = (int)min((int64_t)32, ye - rb);
+        for (int k = 0; k < kmax; ++k) {
+          int64_t vb = __shfl_sync(0xffffffffu, vb_l, k);
+          int64_t ve = vb + __shfl_sync(0xffffffffu, len_l, k);
+          for (int64_t sb = vb; sb < ve; sb += 32 * PAIR_ILP) {
+            int32_t jj[PAIR_ILP];
+            bool past = false;
+#pragma unroll
+            for (int u = 0; u < PAIR_ILP; ++u) {
+              int64_t s_ = sb + lane + 32 * u;
+              jj[u] = s_ < ve ? tl3.U[s_] : 0x7fffffff;
+              if (jj[u] >= i) { jj[u] = -1; past = true; }
+            }
+#pragma unroll
+            for (int u = 0; u < PAIR_ILP; ++u)
+              if (jj[u] >= 0) n17 += (u128)(w.get(jj[u]) - 2);   // x, y are common neighbours of i, j
+            if (__any_sync(0xffffffffu, past)) break;
+          }
         }
       }
     }

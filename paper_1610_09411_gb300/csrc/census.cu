@@ -675,6 +675,57 @@ __device__ __forceinline__ uint32_t tagged_inc(uint32_t* p, uint32_t tag) {
   return ((assumed >> 16) == tag) ? (assumed & 0xffffu) : 0u;
 }
 
+// Walks, for one centre c and one position pu, every k in N(c) cap N(u) below
+// u (a prefix of the list of slot c -> u) and every v in N(c) cap N(k) below u
+// (a prefix of the list of slot c -> k), calling visit(pv) once per pair with
+// pv the position of v in row c.  A warp takes the k's a0, a0 + astep, ...:
+// it fetches 32 of them at a time (lane l the l-th) and scans each v list with
+// WHEEL_ILP independent loads in flight per lane.
+static constexpr int WHEEL_ILP = 4;
+
+template <class Visit>
+__device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t* T, int64_t base, const int32_t* Lu,
+                                            uint32_t lenu, int pu, uint32_t a0, uint32_t astep, Visit&& visit) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t ab = a0; ab < lenu; ab += 32 * astep) {
+    uint32_t a = ab + lane * astep;
+    int64_t ok_l = 0;
+    uint32_t lk_l = 0;
+    bool live = a < lenu, in = false;
+    if (live) {
+      int32_t pk = Lu[a];
+      if (pk < pu) {
+        in = true;
+        ok_l = tl3.offp[base + pk];
+        lk_l = T[base + pk];
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, in);
+    bool done = __any_sync(0xffffffffu, live && !in);   // the k list is sorted: later rounds are above u
+    while (m) {
+      int k = __ffs(m) - 1;
+      m &= m - 1;
+      int64_t ok = __shfl_sync(0xffffffffu, ok_l, k);
+      uint32_t lk = __shfl_sync(0xffffffffu, lk_l, k);
+      for (uint32_t tb = 0; tb < lk; tb += 32 * WHEEL_ILP) {
+        int32_t pv[WHEEL_ILP];
+        bool past = false;
+#pragma unroll
+        for (int u = 0; u < WHEEL_ILP; ++u) {
+          uint32_t t = tb + lane + 32 * u;
+          pv[u] = t < lk ? tl3.P[ok + t] : 0x7fffffff;
+          if (pv[u] >= pu) { pv[u] = -1; past = true; }
+        }
+#pragma unroll
+        for (int u = 0; u < WHEEL_ILP; ++u)
+          if (pv[u] >= 0) visit(pv[u]);
+        if (__any_sync(0xffffffffu, past)) break;
+      }
+    }
+    if (done) break;
+  }
+}
+
 __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ uint32_t scr_all[8][WHEEL_WARP_MAX];
@@ -699,17 +750,7 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uin
       const int32_t* Lu = tl3.P + tl3.offp[base + pu];
       uint32_t tag = (uint32_t)pu + 1;                   // <= 1024: fits the 16-bit tag
       unsigned long long part = 0;
-      for (uint32_t a = 0; a < lenu; ++a) {
-        int32_t pk = Lu[a];
-        if (pk >= pu) break;
-        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
-        uint32_t lenk = T[base + pk];
-        for (uint32_t t = lane; t < lenk; t += 32) {
-          int32_t pv = Lk[t];
-          if (pv >= pu) break;
-          part += tagged_inc(&scr[pv], tag);
-        }
-      }
+      wheel_links(tl3, T, base, Lu, lenu, pu, 0u, 1u, [&](int32_t pv) { part += tagged_inc(&scr[pv], tag); });
       n18 += part;
     }
     __syncwarp();
@@ -757,30 +798,11 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
       if (lenu < 2) continue;
       const int32_t* Lu = tl3.P + tl3.offp[base + pu];
       unsigned long long part = 0;
-      for (uint32_t a = wid; a < lenu; a += nw) {
-        int32_t pk = Lu[a];
-        if (pk >= pu) break;
-        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
-        uint32_t lenk = T[base + pk];
-        for (uint32_t t = lane; t < lenk; t += 32) {
-          int32_t pv = Lk[t];
-          if (pv >= pu) break;
-          part += atomicAdd(&scr[pv], 1u);
-        }
-      }
+      wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw,
+                  [&](int32_t pv) { part += atomicAdd(&scr[pv], 1u); });
       la.v[0] += part;
       __syncthreads();
-      for (uint32_t a = wid; a < lenu; a += nw) {
-        int32_t pk = Lu[a];
-        if (pk >= pu) break;
-        const int32_t* Lk = tl3.P + tl3.offp[base + pk];
-        uint32_t lenk = T[base + pk];
-        for (uint32_t t = lane; t < lenk; t += 32) {
-          int32_t pv = Lk[t];
-          if (pv >= pu) break;
-          scr[pv] = 0;
-        }
-      }
+      wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw, [&](int32_t pv) { scr[pv] = 0; });
       __syncthreads();
     }
     block_item_flush(la, ids, acc, c, sh);

@@ -546,7 +546,10 @@ struct PairCounters {
   }
 };
 
-static constexpr int PAIR_ILP = 4;        // independent accesses in flight per lane
+#ifndef ESC_PAIR_ILP
+#define ESC_PAIR_ILP 8
+#endif
+static constexpr int PAIR_ILP = ESC_PAIR_ILP;   // independent accesses in flight per lane
 
 template <bool NARROW>
 __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
@@ -681,7 +684,10 @@ __device__ __forceinline__ uint32_t tagged_inc(uint32_t* p, uint32_t tag) {
 // pv the position of v in row c.  A warp takes the k's a0, a0 + astep, ...:
 // it fetches 32 of them at a time (lane l the l-th) and scans each v list with
 // WHEEL_ILP independent loads in flight per lane.
-static constexpr int WHEEL_ILP = 4;
+#ifndef ESC_WHEEL_ILP
+#define ESC_WHEEL_ILP 8
+#endif
+static constexpr int WHEEL_ILP = ESC_WHEEL_ILP;
 
 template <class Visit>
 __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t* T, int64_t base, const int32_t* Lu,

@@ -664,10 +664,10 @@ __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long
 // indexed by position.  sum_v C(w, 2) is the sum of the values each increment
 // returns.
 // ============================================================================
-static constexpr int WHEEL_WARP_MAX = 1024;     // centres up to this degree: one warp each
+static constexpr int WHEEL_WARP_MAX = 1024;     // centres up to this degree: warp items
 
-// Counter tagged with the u it belongs to: (tag << 16) | count.  An entry whose
-// tag differs counts as zero, so nothing has to be cleared between u's.
+// Counter tagged with the u it was counted for: (tag << 16) | count.  An entry
+// whose tag differs counts as zero, so nothing has to be cleared between u's.
 __device__ __forceinline__ uint32_t tagged_inc(uint32_t* p, uint32_t tag) {
   uint32_t old = *(volatile uint32_t*)p, assumed;
   do {
@@ -732,34 +732,66 @@ __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t*
   }
 }
 
-__global__ void k_wheels_warp(DevGraph g, int64_t c_end, TriLists tl3, const uint32_t* T, AccSet acc) {
+// Centres up to WHEEL_WARP_MAX: work items are (centre, block of WHEEL_WBLK
+// positions u), pulled by whole warps from a queue, heaviest centres first.
+// Each warp owns a counter array in shared memory whose entries carry the tag
+// of the u they were counted for; a fresh tag per u makes every older entry
+// count as zero, so nothing is cleared between u's or items.
+static constexpr int WHEEL_WBLK = 32;
+
+// item_cnt[k] = number of items of centre c0 - 1 - k (position k in the queue)
+__global__ void k_wheel_warp_counts(DevGraph g, int64_t c0, int64_t* item_cnt) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < c0; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = c0 - 1 - k;
+    int64_t d = g.R[c + 1] - g.R[c];
+    item_cnt[k] = d >= 4 ? (d + WHEEL_WBLK - 1) / WHEEL_WBLK : 0;
+  }
+}
+
+__global__ void k_wheels_warp(DevGraph g, int64_t c0, const int64_t* item_off, unsigned long long* qctr,
+                              TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ uint32_t scr_all[8][WHEEL_WARP_MAX];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   uint32_t* scr = scr_all[wl];
-  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int ids[1] = {ACC_N18};
   LocalAcc<1> la;
   la.zero();
-  for (int64_t k = warp; k < c_end; k += nwarps) {
-    int64_t c = c_end - 1 - k;                          // largest (most work) first
+  for (int i = lane; i < WHEEL_WARP_MAX; i += 32) scr[i] = 0;
+  __syncwarp();
+  uint32_t tag = 0;
+  const int64_t nitems = item_off[c0];
+  while (true) {
+    unsigned long long it_l = 0;
+    if (lane == 0) it_l = atomicAdd(qctr, 1ull);
+    int64_t it = (int64_t)__shfl_sync(0xffffffffu, it_l, 0);
+    if (it >= nitems) break;
+    // queue position of the centre: the last k with item_off[k] <= it
+    int64_t lo = 0, hi = c0;
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (item_off[mid] <= it) lo = mid; else hi = mid;
+    }
+    int64_t c = c0 - 1 - lo;
     int64_t base = g.R[c];
     int d = (int)(g.R[c + 1] - base);
-    if (d < 4) continue;
-    for (int i = lane; i < d; i += 32) scr[i] = 0;       // tags of the previous centre
-    __syncwarp();
+    int u0 = (int)(it - item_off[lo]) * WHEEL_WBLK;
+    int u1 = min(d, u0 + WHEEL_WBLK);
     u128 n18 = 0;
-    for (int pu = 0; pu < d; ++pu) {
+    for (int pu = u0; pu < u1; ++pu) {
       uint32_t lenu = T[base + pu];
       if (lenu < 2) continue;
+      if (++tag == 0x10000u) {                           // tags exhausted: start over from zeroed counters
+        __syncwarp();
+        for (int i = lane; i < WHEEL_WARP_MAX; i += 32) scr[i] = 0;
+        __syncwarp();
+        tag = 1;
+      }
       const int32_t* Lu = tl3.P + tl3.offp[base + pu];
-      uint32_t tag = (uint32_t)pu + 1;                   // <= 1024: fits the 16-bit tag
       unsigned long long part = 0;
       wheel_links(tl3, T, base, Lu, lenu, pu, 0u, 1u, [&](int32_t pv) { part += tagged_inc(&scr[pv], tag); });
       n18 += part;
     }
-    __syncwarp();
     la.v[0] += n18;
     warp_item_flush(la, ids, acc, c);
   }
@@ -785,6 +817,7 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
   while (true) {
     int64_t it = next_item(qctr, nitems, &sh_item);
     if (it < 0) break;
+    it = nitems - 1 - it;                     // heaviest centres first
     // centre of item `it`: the last k with item_off[k] <= it (item_off over centres c0..n-1)
     int64_t lo = 0, hi = g.n - c0;
     while (hi - lo > 1) { int64_t mid = (lo + hi) >> 1; if (item_off[mid] <= it) lo = mid; else hi = mid; }
@@ -1439,6 +1472,12 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * 2 * sms + 16, s);
     ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
   }
+  DevBuf b_wo;                                 // warp wheel items: offsets over centres c0-1 .. 0
+  if (c0 > 0) {
+    ESC_TRY(b_wo.alloc(sizeof(int64_t) * (size_t)(c0 + 1)));
+    (k_wheel_warp_counts<<<grid_for(c0, TPB, sms), TPB, 0, s>>>(g, c0, b_wo.as<int64_t>()), note_launch());
+    ESC_TRY(exclusive_scan_i64(b_wo.as<int64_t>(), b_wo.as<int64_t>(), c0, true, arena, s));
+  }
 
   // ---------------- concurrent phases on forked streams
   // The common-neighbour lists come first (short when alone); then
@@ -1463,8 +1502,12 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (c0 < n)
     (k_wheels_cta<<<2 * sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
                                             b_gs.as<uint32_t>(), gstride, smem_cap, accs), note_launch());
-  if (c0 > 0)
-    (k_wheels_warp<<<grid_for(c0 * 32, 256, sms), 256, 0, s3>>>(g, c0, tl3, T, accs), note_launch());
+  if (c0 > 0) {
+    int per_sm = 1;
+    ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wheels_warp, 256, 0));
+    (k_wheels_warp<<<(unsigned)std::max(1, per_sm) * sms, 256, 0, s3>>>(g, c0, b_wo.as<int64_t>(), ctr + 7, tl3, T,
+                                                                          accs), note_launch());
+  }
   mark(6, 1, s3);
   // pairs (Thms 11, 12); 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
   mark(5, 0, s);

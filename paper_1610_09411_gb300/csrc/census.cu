@@ -522,27 +522,28 @@ struct TriLists {
 // j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
 // per-edge triangle lists).
 // ============================================================================
-// Counters of the pair sweep.  NARROW: two 16-bit counters per 32-bit word
-// (used when every degree is below 2^16, so no W(i,j) can reach 2^16); this
-// halves the per-CTA footprint so more of the counters stay in L2.
-template <bool NARROW>
+// Counters of the pair sweep, tagged with the item they count for: a word is
+// (tag << TB) | count with TB half its width.  Before each increment a
+// fire-and-forget atomicMax with (tag << TB) turns an entry left by an earlier
+// item into a zero count of the current one (a CTA's tags grow with the items
+// it takes), so nothing is cleared between items and no list of touched
+// entries is kept.  32-bit words (16-bit counts) when every degree is below
+// 2^16, so that no W(i,j) can reach 2^16; 64-bit words otherwise.
+template <typename Word>
 struct PairCounters {
-  uint32_t* w;
+  static constexpr int TB = 4 * (int)sizeof(Word);
+  static constexpr Word CMASK = ((Word)1 << TB) - 1;
+  static constexpr uint64_t TAG_MAX = (uint64_t)CMASK;   // largest tag
+  Word* w;
+  Word tagw;                                             // current tag << TB
   __device__ __forceinline__ uint32_t inc(int32_t j) const {
-    if (NARROW) {
-      unsigned sh = (unsigned)(j & 1) << 4;
-      uint32_t old = atomicAdd(&w[j >> 1], 1u << sh);
-      return (old >> sh) & 0xffffu;
-    }
-    return atomicAdd(&w[j], 1u);
+    atomicMax(&w[j], tagw);
+    Word old = atomicAdd(&w[j], (Word)1);
+    return (uint32_t)(old & CMASK);
   }
   __device__ __forceinline__ uint32_t get(int32_t j) const {
-    if (NARROW) return (w[j >> 1] >> ((unsigned)(j & 1) << 4)) & 0xffffu;
-    return w[j];
-  }
-  __device__ __forceinline__ void clear(int32_t j) const {
-    if (NARROW) ((unsigned short*)w)[j] = 0;   // little-endian: half j&1 of word j>>1
-    else w[j] = 0;
+    Word v = w[j];
+    return (v & ~CMASK) == tagw ? (uint32_t)(v & CMASK) : 0u;
   }
 };
 
@@ -551,28 +552,30 @@ struct PairCounters {
 #endif
 static constexpr int PAIR_ILP = ESC_PAIR_ILP;   // independent accesses in flight per lane
 
-template <bool NARROW>
+template <typename Word>
 __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
                         TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  int64_t stride = NARROW ? (ss.n + 1) / 2 : ss.n;
-  PairCounters<NARROW> w{ss.cnt + (int64_t)blockIdx.x * stride};
-  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
-  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
+  PairCounters<Word> w{(Word*)ss.cnt + (int64_t)blockIdx.x * ss.n, (Word)0};
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ids[2] = {ACC_N13, ACC_N17};
   LocalAcc<2> la;
   la.zero();
+  uint64_t tag = 0;                             // items this CTA has taken (the same in every thread)
   while (true) {
     int64_t it = next_item(qctr, item_hi - item_lo, &sh_item);
     if (it < 0) break;
     int64_t i = g.n - 1 - (item_lo + it);
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
     if (e0 - b0 < 2) continue;
+    if (++tag > PairCounters<Word>::TAG_MAX) {  // tags used up: zero the counters, start over
+      for (int64_t t = threadIdx.x; t < ss.n; t += blockDim.x) w.w[t] = 0;
+      __syncthreads();
+      tag = 1;
+    }
+    w.tagw = (Word)tag << PairCounters<Word>::TB;
     u128 n13 = 0, n17 = 0;
-    if (threadIdx.x == 0) *nt = 0;
-    __syncthreads();
     // The warp's lists are fetched 32 at a time (lane k holds the k-th), and
     // each lane keeps PAIR_ILP independent loads and counter operations in
     // flight: the sweep is bound by the latency of scattered accesses.
@@ -595,15 +598,11 @@ __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long
 #pragma unroll
           for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? w.inc(jj[u]) : 1u;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) {
-            n13 += (u128)oo[u] * (oo[u] - 1) / 2;   // zero for old = 0 and 1
-            warp_append(tl, nt, oo[u] == 0, jj[u]);
-          }
+          for (int u = 0; u < PAIR_ILP; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;   // zero for old = 0 and 1
         }
       }
     }
     __syncthreads();
-    unsigned ntc = *nt;
     // diamonds with tip i: for each x in N(i) the triangles {i, x, y} with y
     // above x (a suffix of the position list of slot (x -> i)); their
     // common-neighbour lists are sorted, so the j below i are a prefix
@@ -645,8 +644,6 @@ __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long
         }
       }
     }
-    __syncthreads();
-    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w.clear(tl[t]);
     la.v[0] += n13;
     la.v[1] += n17;
     block_item_flush(la, ids, acc, i, sh);
@@ -1401,21 +1398,17 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
 
   // sweep scratch: one set per concurrent sweep (4-cycles, pairs, 5-cycles x2)
-  DevBuf b_cntA, b_tlA, b_cntB, b_tlB, b_cntC, b_tlC, b_cntD, b_tlD, b_ntA, b_ntB, b_ntC;
+  DevBuf b_cntA, b_tlA, b_cntB, b_cntC, b_tlC, b_cntD, b_tlD, b_ntA, b_ntC;
   size_t sw = sizeof(uint32_t) * (size_t)n * grid_sweep + 16;
   ESC_TRY(b_cntA.alloc(sw)); ESC_TRY(b_tlA.alloc(sw));
-  ESC_TRY(b_cntB.alloc(sw)); ESC_TRY(b_tlB.alloc(sw));
   ESC_TRY(b_cntC.alloc(sw)); ESC_TRY(b_tlC.alloc(sw));
   ESC_TRY(b_cntD.alloc(sw)); ESC_TRY(b_tlD.alloc(sw));
   ESC_TRY(b_ntA.alloc(sizeof(unsigned) * 2 * grid_sweep));
-  ESC_TRY(b_ntB.alloc(sizeof(unsigned) * 2 * grid_sweep));
   ESC_TRY(b_ntC.alloc(sizeof(unsigned) * 2 * grid_sweep));
   cudaMemsetAsync(b_cntA.p, 0, sw, s);
-  cudaMemsetAsync(b_cntB.p, 0, sw, s);
   cudaMemsetAsync(b_cntC.p, 0, sw, s);
   cudaMemsetAsync(b_cntD.p, 0, sw, s);
   SweepScratch ssA{b_cntA.as<uint32_t>(), b_tlA.as<int32_t>(), nullptr, nullptr, b_ntA.as<unsigned>(), n};
-  SweepScratch ssB{b_cntB.as<uint32_t>(), b_tlB.as<int32_t>(), nullptr, nullptr, b_ntB.as<unsigned>(), n};
   SweepScratch ssC{b_cntC.as<uint32_t>(), b_tlC.as<int32_t>(), b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(),
                    b_ntC.as<unsigned>(), n};
 
@@ -1439,6 +1432,12 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
   int64_t maxdeg = n > 0 ? hR[n] - hR[n - 1] : 0;   // the highest rank has the largest degree
+  // pair sweep: tagged counters, 32-bit words when no W(i,j) can reach 2^16
+  const bool pair_narrow = maxdeg < 65536;
+  size_t swB = (pair_narrow ? sizeof(uint32_t) : sizeof(unsigned long long)) * (size_t)n * grid_sweep + 16;
+  ESC_TRY(b_cntB.alloc(swB));
+  cudaMemsetAsync(b_cntB.p, 0, swB, s);
+  SweepScratch ssB{b_cntB.as<uint32_t>(), nullptr, nullptr, nullptr, nullptr, n};
   const int hcap_l = 8192;
   int64_t ghash_cap = pow2_at_least((int)std::max<int64_t>(2 * maxdeg, 2));
   if (2 * maxdeg <= hcap_l) ghash_cap = 2;
@@ -1515,10 +1514,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can);
     // whole warps only: the kernel's reductions shuffle across full warps
     int pthreads = std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
-    if (maxdeg < 65536)
-      (k_pairs<true><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs), note_launch());
+    if (pair_narrow)
+      (k_pairs<uint32_t><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs), note_launch());
     else
-      (k_pairs<false><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs), note_launch());
+      (k_pairs<unsigned long long><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs),
+       note_launch());
   }
   mark(5, 1, s);
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)

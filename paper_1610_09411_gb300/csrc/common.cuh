@@ -200,47 +200,6 @@ __device__ __forceinline__ void warp_append(int32_t* list, unsigned* n, bool tak
   if (take) list[base + __popc(b & ((1u << lane) - 1u))] = j;
 }
 
-// ---------------------------------------------------------------- block scans
-// Exclusive prefix sum of one u32 per thread over the block (blockDim a
-// multiple of 32, at most 1024).  Returns the thread's prefix and sets *total
-// to the block's sum.  `wsum` must hold 32 words.  All threads must call it.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* wsum, uint32_t* total) {
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  __syncthreads();                 // wsum may still be read from the previous call
-  if (lane == 31) wsum[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t t = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < nw) wsum[lane] = t;
-  }
-  __syncthreads();
-  *total = wsum[nw - 1];
-  return (wid ? wsum[wid - 1] : 0u) + x - v;
-}
-
-// Segment of flat index f: the last s in [0, nseg) with scan[s] <= f, where
-// scan holds the exclusive prefix sums of the segment lengths (scan[0] = 0).
-// Empty segments are never returned for an f below the total.
-__device__ __forceinline__ int segment_of(const uint32_t* scan, int nseg, uint32_t f) {
-  int lo = 0, hi = nseg;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (scan[mid] <= f) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 // ---------------------------------------------------------------- status word
 // Device-side error flags (no traps): kernels record the first problem they
 // meet here and skip the offending access; the host turns a non-zero word

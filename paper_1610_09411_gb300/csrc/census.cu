@@ -428,6 +428,133 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
   final_flush(la, ids, acc, sh);
 }
 
+// Small out-neighbourhoods (d+ <= 32 and d- <= CLQ_WARP_DIN): one warp per
+// vertex x, everything in the warp's shared memory.  Lane a holds v_a, the
+// a-th vertex of N+(x); row a of the bit matrix of G[N+(x)] is one 64-bit word
+// and D_a (the in-neighbours of x adjacent to v_a) at most CLQ_WARP_DIN / 64.
+// The sums and per-edge counts are those of k_clique_large.
+static constexpr int CLQ_WARP_DIN = 512;
+static constexpr int CLQ_WARPS = 8;            // warps per block
+static constexpr int CLQ_ILP = 4;
+
+__global__ void __launch_bounds__(CLQ_WARPS * 32) k_clique_warp(DevGraph g, const int32_t* items, int64_t nitems,
+                                                                unsigned long long* qctr, const uint32_t* T,
+                                                                unsigned long long* K4e, AccSet acc) {
+  __shared__ u128 sh[32];
+  __shared__ int32_t sL[CLQ_WARPS][32];
+  __shared__ uint32_t sT[CLQ_WARPS][32];
+  __shared__ unsigned long long sB[CLQ_WARPS][32], sK[CLQ_WARPS][32];
+  __shared__ unsigned long long sD[CLQ_WARPS][32][CLQ_WARP_DIN / 64];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  int32_t* L = sL[wl];
+  unsigned long long* Bw = sB[wl];
+  unsigned long long* K = sK[wl];
+  const int ids[5] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21};
+  LocalAcc<5> la;
+  la.zero();
+  // position of vertex key in N+(x) (sorted, padded with INT32_MAX), or -1
+  auto find = [&](int32_t key) -> int {
+    int lo = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+      if (L[lo + st] <= key) lo += st;
+    return L[lo] == key ? lo : -1;
+  };
+  while (true) {
+    unsigned long long it_l = 0;
+    if (lane == 0) it_l = atomicAdd(qctr, 1ull);
+    int64_t it = (int64_t)__shfl_sync(0xffffffffu, it_l, 0);
+    if (it >= nitems) break;
+    int64_t x = items[it];
+    int64_t o = g.op[x], ib = g.R[x];
+    int d = (int)(g.R[x + 1] - o);
+    int din = (int)(o - ib);
+    int DW = (din + 63) >> 6;
+    int32_t va = lane < d ? g.C[o + lane] : 0x7fffffff;
+    L[lane] = va;
+    sT[wl][lane] = lane < d ? T[o + lane] : 0u;
+    Bw[lane] = 0;
+    K[lane] = 0;
+    for (int w = 0; w < DW; ++w) sD[wl][lane][w] = 0;
+    __syncwarp();
+    // rows of G[N+(x)]: lane a scans N+(v_a) (everything there is above v_a)
+    int64_t qa0 = 0, qa1 = 0;
+    if (lane < d) {
+      qa0 = g.op[va];
+      qa1 = g.R[va + 1];
+    }
+    for (int64_t q = qa0; q < qa1; q += CLQ_ILP) {
+      int32_t ww[CLQ_ILP];
+#pragma unroll
+      for (int u = 0; u < CLQ_ILP; ++u) ww[u] = q + u < qa1 ? g.C[q + u] : 0x7fffffff;
+#pragma unroll
+      for (int u = 0; u < CLQ_ILP; ++u) {
+        int b = ww[u] == 0x7fffffff ? -1 : find(ww[u]);
+        if (b >= 0) {
+          atomicOr(&Bw[lane], 1ull << b);
+          atomicOr(&Bw[b], 1ull << lane);
+        }
+      }
+    }
+    // D: in-neighbour y (index k) marks bit k of D_a for every v_a in N+(y)
+    for (int k = lane; k < din; k += 32) {
+      int32_t y = g.C[ib + k];
+      int64_t q1 = g.R[y + 1];
+      for (int64_t q = g.op[y]; q < q1; q += CLQ_ILP) {
+        int32_t ww[CLQ_ILP];
+#pragma unroll
+        for (int u = 0; u < CLQ_ILP; ++u) ww[u] = q + u < q1 ? g.C[q + u] : 0x7fffffff;
+#pragma unroll
+        for (int u = 0; u < CLQ_ILP; ++u) {
+          int a = ww[u] == 0x7fffffff ? -1 : find(ww[u]);
+          if (a >= 0) atomicOr(&sD[wl][a][k >> 6], 1ull << (k & 63));
+        }
+      }
+    }
+    __syncwarp();
+    // edges (a, b) of G[N+(x)], a < b: lane a scans N+(v_a) again for the slot
+    if (lane < d) {
+      unsigned long long dx = (unsigned long long)(g.R[x + 1] - g.R[x]);
+      unsigned long long dva = (unsigned long long)(g.R[va + 1] - g.R[va]);
+      unsigned long long ra = Bw[lane], k4a = 0, txa = sT[wl][lane];
+      for (int64_t q = qa0; q < qa1; ++q) {
+        int32_t w = g.C[q];
+        int b = find(w);
+        if (b < 0) continue;
+        unsigned long long cm = ra & Bw[b];
+        unsigned long long alpha = (unsigned long long)__popcll(cm), beta = 0, k5 = 0;
+        for (int t = 0; t < DW; ++t) beta += (unsigned long long)__popcll(sD[wl][lane][t] & sD[wl][b][t]);
+        // 5-cliques at the three lowest vertices x, v_a, v_b: every c in the
+        // common neighbourhood above b, then every l adjacent to a, b, c above c
+        unsigned long long cm2 = cm & (~0ull << (b + 1));
+        while (cm2) {
+          int c = __ffsll((long long)cm2) - 1;
+          cm2 &= cm2 - 1;
+          k5 += (unsigned long long)__popcll(cm & Bw[c] & (~0ull << (c + 1)));
+        }
+        unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
+        unsigned long long tab = T[q], txb = sT[wl][b];
+        la.v[0] += alpha;                                         // 3 x K4
+        la.v[1] += ch2(alpha + beta);                             // N20
+        la.v[2] += (u128)(tab - 1) * (dx - 2) + (u128)(txb - 1) * (dva - 2) + (u128)(txa - 1) * (dvb - 2);   // N10
+        la.v[3] += (u128)(txa - 1) * (txb - 1) + (u128)(txa - 1) * (tab - 1) + (u128)(txb - 1) * (tab - 1);  // N16
+        la.v[4] += k5;                                            // N21
+        if (alpha) {
+          atomicAdd(&K4e[q], alpha);
+          atomicAdd(&K[b], alpha);
+          k4a += alpha;
+        }
+      }
+      if (k4a) atomicAdd(&K[lane], k4a);
+    }
+    __syncwarp();
+    if (lane < d && K[lane]) atomicAdd(&K4e[o + lane], K[lane] / 2);
+    warp_item_flush(la, ids, acc, x);
+    __syncwarp();
+  }
+  final_flush(la, ids, acc, sh);
+}
+
 // ============================================================================
 // Thm 5: 4-cycles.  For the highest vertex i and each j < i,
 // w(i,j) = |{k in N(i) cap N(j) : k < i}| (out-wedges and in-out wedges);
@@ -1161,14 +1288,23 @@ __global__ void k_graph_sizes(const int64_t* voff, const int64_t* rp, int num_gr
 }
 
 // item lists of pass A/B: vertices by out-degree class
-__global__ void k_split_items(DevGraph g, int32_t* small, int32_t* large, unsigned long long* cnts, int small_max) {
+// small / large: d+ up to small_max or above (vertices with d+ >= 2); the
+// small ones are also split by d- for the clique pass: up to warp_din in wsmall
+// (one warp each), the rest in csmall (one CTA each).
+__global__ void k_split_items(DevGraph g, int32_t* small, int32_t* large, int32_t* wsmall, int32_t* csmall,
+                              unsigned long long* cnts, int small_max, int warp_din) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < g.n; k += stride) {
     int64_t x = g.n - 1 - k;
     int64_t d = g.R[x + 1] - g.op[x];
     if (d < 2) continue;
-    if (d <= small_max) small[atomicAdd(&cnts[0], 1ull)] = (int32_t)x;
-    else large[atomicAdd(&cnts[1], 1ull)] = (int32_t)x;
+    if (d <= small_max) {
+      small[atomicAdd(&cnts[0], 1ull)] = (int32_t)x;
+      if (g.op[x] - g.R[x] <= warp_din) wsmall[atomicAdd(&cnts[2], 1ull)] = (int32_t)x;
+      else csmall[atomicAdd(&cnts[3], 1ull)] = (int32_t)x;
+    } else {
+      large[atomicAdd(&cnts[1], 1ull)] = (int32_t)x;
+    }
   }
 }
 
@@ -1338,13 +1474,17 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (n > 0) (k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, accs), note_launch());
 
   // ---------------- item lists for the out-neighbourhood passes
-  DevBuf b_small, b_large, b_dims;
+  DevBuf b_small, b_large, b_wsmall, b_csmall, b_dims;
   ESC_TRY(b_small.alloc(sizeof(int32_t) * (n + 1)));
   ESC_TRY(b_large.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_wsmall.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_csmall.alloc(sizeof(int32_t) * (n + 1)));
   ESC_TRY(b_dims.alloc(sizeof(unsigned long long) * 2));
   cudaMemsetAsync(b_dims.p, 0, sizeof(unsigned long long) * 2, s);
   if (n > 0) {
-    (k_split_items<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), b_large.as<int32_t>(), ctr, SMALL_DPLUS), note_launch());
+    (k_split_items<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), b_large.as<int32_t>(),
+                                                          b_wsmall.as<int32_t>(), b_csmall.as<int32_t>(), ctr,
+                                                          SMALL_DPLUS, CLQ_WARP_DIN), note_launch());
     (k_clique_dims<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_dims.as<unsigned long long>()), note_launch());
   }
   unsigned long long hcnt[16] = {0}, dims[2] = {0, 0};
@@ -1352,6 +1492,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   cudaMemcpyAsync(dims, b_dims.p, sizeof(dims), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
   int64_t nsmall = (int64_t)hcnt[0], nlarge = (int64_t)hcnt[1];
+  int64_t nwsmall = (int64_t)hcnt[2], ncsmall = (int64_t)hcnt[3];
   int dmax = (int)dims[1];
   if (dmax < SMALL_DPLUS + 1) dmax = SMALL_DPLUS + 1;
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
@@ -1381,11 +1522,15 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // pass B inputs
-  int64_t nitems_b = nsmall + nlarge;
+  // CTA items: every large out-neighbourhood, then the small ones with many
+  // in-neighbours; the other small ones go to the warp kernel
+  int64_t nitems_b = nlarge + ncsmall;
   DevBuf b_items, b_D;
   ESC_TRY(b_items.alloc(sizeof(int32_t) * (nitems_b + 1)));
   if (nlarge) cudaMemcpyAsync(b_items.p, b_large.p, sizeof(int32_t) * nlarge, cudaMemcpyDeviceToDevice, s);
-  if (nsmall) cudaMemcpyAsync(b_items.as<int32_t>() + nlarge, b_small.p, sizeof(int32_t) * nsmall, cudaMemcpyDeviceToDevice, s);
+  if (ncsmall)
+    cudaMemcpyAsync(b_items.as<int32_t>() + nlarge, b_csmall.p, sizeof(int32_t) * ncsmall, cudaMemcpyDeviceToDevice,
+                    s);
   int W_cap = (dmax + 63) >> 6;
   int hcap_b = pow2_at_least(2 * dmax);
   size_t smem_b = sizeof(uint64_t) * ((size_t)dmax * W_cap + dmax) + sizeof(int32_t) * (2 * (size_t)hcap_b) +
@@ -1526,6 +1671,13 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (nitems_b > 0)
     (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), 512, smem_b, s1>>>(
         g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, dmax, d_status), note_launch());
+  if (nwsmall > 0) {
+    int per_sm = 1;
+    ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_warp, CLQ_WARPS * 32, 0));
+    unsigned grid_w = (unsigned)std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, (nwsmall + CLQ_WARPS - 1) / CLQ_WARPS);
+    (k_clique_warp<<<grid_w, CLQ_WARPS * 32, 0, s1>>>(g, b_wsmall.as<int32_t>(), nwsmall, ctr + 8, T, K4e, accs),
+     note_launch());
+  }
   if (n > 0) {
     (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e), note_launch());
     (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e, K4v, 3), note_launch());

@@ -562,6 +562,11 @@ __global__ void __launch_bounds__(CLQ_WARPS * 32) k_clique_warp(DevGraph g, cons
 // (i,k), (k,j) and vertex k; every j adds C(w,2) to vertices i and j.
 // CTA per i, dense per-CTA counters over j with a touched list.
 // ============================================================================
+#ifndef ESC_PAIR_ILP
+#define ESC_PAIR_ILP 8
+#endif
+static constexpr int PAIR_ILP = ESC_PAIR_ILP;   // independent accesses in flight per lane (sweeps)
+
 struct SweepScratch {
   uint32_t* cnt;       // per CTA: n counters (kept zero between items)
   int32_t* touched;    // per CTA: n entries
@@ -588,13 +593,28 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
     if (e0 == b0) continue;           // no lower neighbours
     if (threadIdx.x == 0) *nt = 0;
     __syncthreads();
-    // pass 1: wedge counts
-    for (int64_t p = b0 + wid; p < e0; p += nw) {
-      int32_t k = g.C[p];
-      int64_t kb = g.R[k], ke = g.rev[p];       // N(k) below i
-      for (int64_t q = kb + lane; q < ke; q += 32) {
-        int32_t j = g.C[q];
-        warp_append(tl, nt, atomicAdd(&w[j], 1u) == 0, j);
+    // pass 1: wedge counts.  The lists N(k) below i are fetched 32 per warp
+    // (lane l the l-th), PAIR_ILP entries in flight per lane.
+    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
+      int64_t p = pbase + (int64_t)lane * nw;
+      int64_t kb_l = 0, ke_l = 0;
+      if (p < e0) {
+        kb_l = g.R[g.C[p]];
+        ke_l = g.rev[p];                        // N(k) below i ends at the slot of i
+      }
+      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
+      for (int kk = 0; kk < kmax; ++kk) {
+        int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
+        for (int64_t q = kb + lane; q < ke; q += 32 * PAIR_ILP) {
+          int32_t jj[PAIR_ILP];
+          uint32_t oo[PAIR_ILP];
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? atomicAdd(&w[jj[u]], 1u) : 1u;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) warp_append(tl, nt, oo[u] == 0, jj[u]);
+        }
       }
     }
     __syncthreads();
@@ -611,18 +631,38 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       if (acc.vg) acc_add(acc_of(acc, i), ACC_C4, tot);
       else c4sum += tot;
     }
-    // pass 3: per-edge counts
-    for (int64_t p = b0 + wid; p < e0; p += nw) {
-      int32_t k = g.C[p];
-      int64_t kb = g.R[k], ke = g.rev[p];
-      unsigned long long sk = 0;
-      for (int64_t q = kb + lane; q < ke; q += 32) {
-        int32_t j = g.C[q];
-        unsigned long long c = w[j] - 1;
-        if (c) { atomicAdd(&C4raw[q], c); sk += c; }
+    // pass 3: per-edge counts, the lists fetched as in pass 1
+    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
+      int64_t p_l = pbase + (int64_t)lane * nw;
+      int64_t kb_l = 0, ke_l = 0;
+      int32_t k_l = 0;
+      if (p_l < e0) {
+        k_l = g.C[p_l];
+        kb_l = g.R[k_l];
+        ke_l = g.rev[p_l];
       }
-      sk = warp_sum_u64(sk);
-      if (lane == 0 && sk) { atomicAdd(&C4raw[p], sk); atomicAdd(&C4v[k], sk); }
+      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
+      for (int kk = 0; kk < kmax; ++kk) {
+        int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
+        unsigned long long sk = 0;
+        for (int64_t q = kb + lane; q < ke; q += 32 * PAIR_ILP) {
+          int32_t jj[PAIR_ILP];
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) {
+            if (jj[u] < 0) continue;
+            unsigned long long c = w[jj[u]] - 1;
+            if (c) { atomicAdd(&C4raw[q + 32 * u], c); sk += c; }
+          }
+        }
+        sk = warp_sum_u64(sk);
+        int32_t k = __shfl_sync(0xffffffffu, k_l, kk);
+        if (lane == 0 && sk) {
+          atomicAdd(&C4raw[pbase + (int64_t)kk * nw], sk);
+          atomicAdd(&C4v[k], sk);
+        }
+      }
     }
     __syncthreads();
     for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
@@ -649,7 +689,7 @@ struct TriLists {
 // j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
 // per-edge triangle lists).
 // ============================================================================
-// Counters of the pair sweep, tagged with the item they count for: a word is
+// Counters of the pair and 5-cycle sweeps, tagged with the item they count for: a word is
 // (tag << TB) | count with TB half its width.  Before each increment a
 // fire-and-forget atomicMax with (tag << TB) turns an entry left by an earlier
 // item into a zero count of the current one (a CTA's tags grow with the items
@@ -657,7 +697,7 @@ struct TriLists {
 // entries is kept.  32-bit words (16-bit counts) when every degree is below
 // 2^16, so that no W(i,j) can reach 2^16; 64-bit words otherwise.
 template <typename Word>
-struct PairCounters {
+struct TaggedCounters {
   static constexpr int TB = 4 * (int)sizeof(Word);
   static constexpr Word CMASK = ((Word)1 << TB) - 1;
   static constexpr uint64_t TAG_MAX = (uint64_t)CMASK;   // largest tag
@@ -668,23 +708,23 @@ struct PairCounters {
     Word old = atomicAdd(&w[j], (Word)1);
     return (uint32_t)(old & CMASK);
   }
+  __device__ __forceinline__ void add(int32_t j) const {    // the same without the old value
+    atomicMax(&w[j], tagw);
+    atomicAdd(&w[j], (Word)1);
+  }
   __device__ __forceinline__ uint32_t get(int32_t j) const {
     Word v = w[j];
     return (v & ~CMASK) == tagw ? (uint32_t)(v & CMASK) : 0u;
   }
 };
 
-#ifndef ESC_PAIR_ILP
-#define ESC_PAIR_ILP 8
-#endif
-static constexpr int PAIR_ILP = ESC_PAIR_ILP;   // independent accesses in flight per lane
 
 template <typename Word>
 __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
                         TriLists tl3, const uint32_t* T, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  PairCounters<Word> w{(Word*)ss.cnt + (int64_t)blockIdx.x * ss.n, (Word)0};
+  TaggedCounters<Word> w{(Word*)ss.cnt + (int64_t)blockIdx.x * ss.n, (Word)0};
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ids[2] = {ACC_N13, ACC_N17};
   LocalAcc<2> la;
@@ -696,12 +736,12 @@ __global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long
     int64_t i = g.n - 1 - (item_lo + it);
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
     if (e0 - b0 < 2) continue;
-    if (++tag > PairCounters<Word>::TAG_MAX) {  // tags used up: zero the counters, start over
+    if (++tag > TaggedCounters<Word>::TAG_MAX) {  // tags used up: zero the counters, start over
       for (int64_t t = threadIdx.x; t < ss.n; t += blockDim.x) w.w[t] = 0;
       __syncthreads();
       tag = 1;
     }
-    w.tagw = (Word)tag << PairCounters<Word>::TB;
+    w.tagw = (Word)tag << TaggedCounters<Word>::TB;
     u128 n13 = 0, n17 = 0;
     // The warp's lists are fetched 32 at a time (lane k holds the k-th), and
     // each lane keeps PAIR_ILP independent loads and counter operations in
@@ -981,54 +1021,111 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
 // The paths whose own a or b is counted by w' are the directed tailed
 // triangles, subtracted through ACC_N8Z (pass A).
 // ============================================================================
-__global__ void k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss, AccSet acc) {
+template <typename Word>
+__global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
+                                                   AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  uint32_t* wp = ss.cnt + (int64_t)blockIdx.x * ss.n;
-  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
-  uint32_t* p2 = ss.cnt2 + (int64_t)blockIdx.x * ss.n;
+  TaggedCounters<Word> wp{(Word*)ss.cnt + (int64_t)blockIdx.x * ss.n, (Word)0};   // w'(i, .)
+  uint32_t* p2 = ss.cnt2 + (int64_t)blockIdx.x * ss.n;                            // P2(i, .), with a list
   int32_t* tl2 = ss.touched2 + (int64_t)blockIdx.x * ss.n;
   unsigned* nt = ss.ntouched + 2 * blockIdx.x;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ids[1] = {ACC_N8M};
   LocalAcc<1> la;
   la.zero();
+  uint32_t tag = 0;                             // items this CTA has taken (the same in every thread)
   while (true) {
     int64_t it = next_item(qctr, g.n, &sh_item);
     if (it < 0) break;
     int64_t i = g.n - 1 - it;
     int64_t b0 = g.R[i], o = g.op[i], e0 = g.R[i + 1];
     if (o == b0) continue;                      // needs an in-neighbour a
-    if (threadIdx.x == 0) { nt[0] = 0; nt[1] = 0; }
+    if (++tag > TaggedCounters<Word>::TAG_MAX) {   // tags used up: zero the counters, start over
+      for (int64_t t = threadIdx.x; t < ss.n; t += blockDim.x) wp.w[t] = 0;
+      tag = 1;
+    }
+    wp.tagw = (Word)tag << TaggedCounters<Word>::TB;
+    if (threadIdx.x == 0) nt[1] = 0;
     __syncthreads();
-    // w'(i, .): c < i -> every j in N(c); c > i -> j in N+(c)
-    for (int64_t p = b0 + wid; p < e0; p += nw) {
-      int32_t c = g.C[p];
-      int64_t cb = (p < o) ? g.R[c] : g.op[c], ce = g.R[c + 1];
-      for (int64_t q = cb + lane; q < ce; q += 32) {
-        int32_t j = g.C[q];
-        warp_append(tl, &nt[0], j != i && atomicAdd(&wp[j], 1u) == 0, j);
+    // w'(i, .): c < i -> every j in N(c); c > i -> j in N+(c).  Lists are
+    // fetched 32 per warp (lane k the k-th), PAIR_ILP entries in flight per lane.
+    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
+      int64_t p = pbase + (int64_t)lane * nw;
+      int64_t cb_l = 0, ce_l = 0;
+      if (p < e0) {
+        int32_t c = g.C[p];
+        cb_l = (p < o) ? g.R[c] : g.op[c];
+        ce_l = g.R[c + 1];
+      }
+      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
+      for (int k = 0; k < kmax; ++k) {
+        int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
+        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
+          int32_t jj[PAIR_ILP];
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u)
+            if (jj[u] != i) wp.add(jj[u]);
+        }
       }
     }
-    // P2(i, .)
-    for (int64_t p = b0 + wid; p < o; p += nw) {
-      int32_t a = g.C[p];
-      for (int64_t q = g.op[a] + lane; q < g.R[a + 1]; q += 32) {
-        int32_t b = g.C[q];
-        warp_append(tl2, &nt[1], b != i && atomicAdd(&p2[b], 1u) == 0, b);
+    // P2(i, .): a in N-(i), b in N+(a)
+    for (int64_t pbase = b0 + wid; pbase < o; pbase += (int64_t)nw * 32) {
+      int64_t p = pbase + (int64_t)lane * nw;
+      int64_t cb_l = 0, ce_l = 0;
+      if (p < o) {
+        int32_t a = g.C[p];
+        cb_l = g.op[a];
+        ce_l = g.R[a + 1];
+      }
+      int kmax = (int)min((int64_t)32, (o - pbase + nw - 1) / nw);
+      for (int k = 0; k < kmax; ++k) {
+        int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
+        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
+          int32_t bb[PAIR_ILP];
+          uint32_t oo[PAIR_ILP];
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) bb[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) oo[u] = bb[u] != i ? atomicAdd(&p2[bb[u]], 1u) : 1u;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) warp_append(tl2, &nt[1], oo[u] == 0, bb[u]);
+        }
       }
     }
     __syncthreads();
-    unsigned n1 = nt[0], n2 = nt[1];
-    for (unsigned t = wid; t < n2; t += nw) {
-      int32_t b = tl2[t];
-      unsigned long long s = 0;
-      for (int64_t q = g.op[b] + lane; q < g.R[b + 1]; q += 32) s += wp[g.C[q]];
-      s = warp_sum_u64(s);
-      if (lane == 0) la.v[0] += (u128)s * p2[b];
+    unsigned n2 = nt[1];
+    // sum over the distinct b of P2(i, b) * sum_{j in N+(b)} w'(i, j); the
+    // b's are fetched 32 per warp
+    for (unsigned tb = (unsigned)wid * 32; tb < n2; tb += (unsigned)nw * 32) {
+      unsigned t = tb + lane;
+      int64_t cb_l = 0, ce_l = 0;
+      uint32_t pk_l = 0;
+      if (t < n2) {
+        int32_t b = tl2[t];
+        cb_l = g.op[b];
+        ce_l = g.R[b + 1];
+        pk_l = p2[b];
+      }
+      int kmax = (int)min(32u, n2 - tb);
+      for (int k = 0; k < kmax; ++k) {
+        int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
+        uint32_t pk = __shfl_sync(0xffffffffu, pk_l, k);
+        unsigned long long s_ = 0;
+        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
+          int32_t jj[PAIR_ILP];
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : -1;
+#pragma unroll
+          for (int u = 0; u < PAIR_ILP; ++u)
+            if (jj[u] >= 0) s_ += wp.get(jj[u]);
+        }
+        la.v[0] += (u128)s_ * pk;
+      }
     }
     __syncthreads();
-    for (unsigned t = threadIdx.x; t < n1; t += blockDim.x) wp[tl[t]] = 0;
     for (unsigned t = threadIdx.x; t < n2; t += blockDim.x) p2[tl2[t]] = 0;
     block_item_flush(la, ids, acc, i, sh);
     __syncthreads();
@@ -1542,20 +1639,17 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
   CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
 
-  // sweep scratch: one set per concurrent sweep (4-cycles, pairs, 5-cycles x2)
-  DevBuf b_cntA, b_tlA, b_cntB, b_cntC, b_tlC, b_cntD, b_tlD, b_ntA, b_ntC;
+  // sweep scratch: one set per concurrent sweep (4-cycles; pairs and the
+  // tagged 5-cycle counters are sized below, once the largest degree is known)
+  DevBuf b_cntA, b_tlA, b_cntB, b_cntC, b_cntD, b_tlD, b_ntA, b_ntC;
   size_t sw = sizeof(uint32_t) * (size_t)n * grid_sweep + 16;
   ESC_TRY(b_cntA.alloc(sw)); ESC_TRY(b_tlA.alloc(sw));
-  ESC_TRY(b_cntC.alloc(sw)); ESC_TRY(b_tlC.alloc(sw));
   ESC_TRY(b_cntD.alloc(sw)); ESC_TRY(b_tlD.alloc(sw));
   ESC_TRY(b_ntA.alloc(sizeof(unsigned) * 2 * grid_sweep));
   ESC_TRY(b_ntC.alloc(sizeof(unsigned) * 2 * grid_sweep));
   cudaMemsetAsync(b_cntA.p, 0, sw, s);
-  cudaMemsetAsync(b_cntC.p, 0, sw, s);
   cudaMemsetAsync(b_cntD.p, 0, sw, s);
   SweepScratch ssA{b_cntA.as<uint32_t>(), b_tlA.as<int32_t>(), nullptr, nullptr, b_ntA.as<unsigned>(), n};
-  SweepScratch ssC{b_cntC.as<uint32_t>(), b_tlC.as<int32_t>(), b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(),
-                   b_ntC.as<unsigned>(), n};
 
   // common-neighbour list offsets and sizes
   DevBuf b_off, b_offp, b_U, b_P, b_gh;
@@ -1577,12 +1671,16 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
   int64_t maxdeg = n > 0 ? hR[n] - hR[n - 1] : 0;   // the highest rank has the largest degree
-  // pair sweep: tagged counters, 32-bit words when no W(i,j) can reach 2^16
+  // pair and 5-cycle sweeps: tagged counters, 32-bit words when no count
+  // (W(i,j) or w'(i,j), both at most a degree) can reach 2^16
   const bool pair_narrow = maxdeg < 65536;
   size_t swB = (pair_narrow ? sizeof(uint32_t) : sizeof(unsigned long long)) * (size_t)n * grid_sweep + 16;
   ESC_TRY(b_cntB.alloc(swB));
+  ESC_TRY(b_cntC.alloc(swB));
   cudaMemsetAsync(b_cntB.p, 0, swB, s);
+  cudaMemsetAsync(b_cntC.p, 0, swB, s);
   SweepScratch ssB{b_cntB.as<uint32_t>(), nullptr, nullptr, nullptr, nullptr, n};
+  SweepScratch ssC{b_cntC.as<uint32_t>(), nullptr, b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(), b_ntC.as<unsigned>(), n};
   const int hcap_l = 8192;
   int64_t ghash_cap = pow2_at_least((int)std::max<int64_t>(2 * maxdeg, 2));
   if (2 * maxdeg <= hcap_l) ghash_cap = 2;
@@ -1692,7 +1790,12 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(3, 1, s2);
   // 5-cycles (Thm 13)
   mark(7, 0, s4);
-  if (n > 0) (k_cycles5<<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, ssC, accs), note_launch());
+  if (n > 0) {
+    if (pair_narrow)
+      (k_cycles5<uint32_t><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, ssC, accs), note_launch());
+    else
+      (k_cycles5<unsigned long long><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, ssC, accs), note_launch());
+  }
   mark(7, 1, s4);
   ESC_TRY(ss_all.join_into(s));
 

@@ -415,7 +415,7 @@ def main():
     esc.escape_set_options(h, False, 0, True)
     esc.escape_census5(h)
     alone_phase = esc.escape_last_phase_ms(h)
-    esc.escape_set_options(h, False, 0, False)
+    esc.escape_set_options(h, False, 0, None)
     total_ms = slowest_rank_ms(total_ms, world, "cuda")
     ms_per_step = total_ms / args.steps
     value = replica_value(world, g.m, ms_per_step)

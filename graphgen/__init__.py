@@ -179,6 +179,21 @@ def complete_bipartite(a: int, b: int) -> Graph:
     return from_edges(a + b, i.ravel(), j.ravel(), f"K{a},{b}")
 
 
+def two_hubs(leaves: int = 65600) -> Graph:
+    """Two adjacent hubs 0 and 1 joined to every leaf 2 .. leaves+1, a path over
+    the first 400 leaves and a clique on the next 19: two vertices of degree
+    above 2^16 whose common neighbourhood also exceeds 2^16."""
+    s = [np.zeros(leaves, np.int64), np.ones(leaves, np.int64), np.array([0])]
+    d = [np.arange(2, leaves + 2), np.arange(2, leaves + 2), np.array([1])]
+    p = np.arange(2, 401)
+    s.append(p)
+    d.append(p + 1)
+    i, j = np.triu_indices(19, 1)
+    s.append(402 + i)
+    d.append(402 + j)
+    return from_edges(leaves + 2, np.concatenate(s), np.concatenate(d), f"two_hubs{leaves}")
+
+
 def petersen() -> Graph:
     outer = [(i, (i + 1) % 5) for i in range(5)]
     spokes = [(i, i + 5) for i in range(5)]

@@ -123,10 +123,13 @@ escape_status escape_per_element(escape_graph* g, uint64_t* tri_e, uint64_t* c4_
 
 /* Options: keep_per_element (0/1) makes escape_census5 retain the arrays
  * read by escape_per_element; cta_per_sm sets the persistent-CTA count of the
- * sweep kernels (0 = default, 1..8); serial_phases (0/1) runs every phase on
- * the caller's stream one after another instead of overlapping the
- * independent sweeps on side streams (the results are the same; the phase
- * times of escape_last_phase_ms are then each kernel's time alone). */
+ * sweep kernels (0 = default, 1..8); serial_phases 1 runs every phase on the
+ * caller's stream one after another, 0 overlaps the independent sweeps on
+ * side streams, and a negative value (the default) chooses by size: one after
+ * another for graphs of at least 2^24 adjacency entries (2 x edges), where
+ * each sweep fills the GPU alone, overlapped below.  The results are the
+ * same either way; with the phases one after another, the times of
+ * escape_last_phase_ms are each kernel's time alone. */
 escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_per_sm, int serial_phases);
 
 /*

@@ -689,59 +689,92 @@ struct TriLists {
 // j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
 // per-edge triangle lists).
 // ============================================================================
-// Counters of the pair and 5-cycle sweeps, tagged with the item they count for: a word is
-// (tag << TB) | count with TB half its width.  Before each increment a
-// fire-and-forget atomicMax with (tag << TB) turns an entry left by an earlier
-// item into a zero count of the current one (a CTA's tags grow with the items
-// it takes), so nothing is cleared between items and no list of touched
-// entries is kept.  32-bit words (16-bit counts) when every degree is below
-// 2^16, so that no W(i,j) can reach 2^16; 64-bit words otherwise.
-template <typename Word>
+// Counters of the pair and 5-cycle sweeps, tagged with the item they count
+// for.  Before each increment a fire-and-forget atomicMax with the current tag
+// turns an entry left by an earlier item into a zero count of the current one
+// (a CTA's tags grow with the items it takes), so nothing is cleared between
+// items and no list of touched entries is kept.  Every count at j (W(i,j) or
+// w'(i,j)) is at most d(j), so the ranks below jbig, the first of degree
+// >= 2^16, keep (tag << 16) | count in 32-bit words; the few ranks from jbig on
+// keep (tag << 32) | count in a 64-bit side array.
+struct TagScratch {
+  uint32_t* w;              // per CTA: jbig words
+  unsigned long long* wb;   // per CTA: n - jbig words
+  int64_t jbig, n;
+};
+
+template <bool BIG>   // BIG: some rank has degree >= 2^16 (jbig < n)
 struct TaggedCounters {
-  static constexpr int TB = 4 * (int)sizeof(Word);
-  static constexpr Word CMASK = ((Word)1 << TB) - 1;
-  static constexpr uint64_t TAG_MAX = (uint64_t)CMASK;   // largest tag
-  Word* w;
-  Word tagw;                                             // current tag << TB
+  static constexpr uint32_t TAG_MAX = 0xffffu;   // largest tag of the 32-bit words
+  uint32_t* w;
+  unsigned long long* wb;
+  int32_t jbig;
+  uint32_t tag;
+  __device__ TaggedCounters(const TagScratch& ts) {
+    w = ts.w + (int64_t)blockIdx.x * ts.jbig;
+    wb = ts.wb + (int64_t)blockIdx.x * (ts.n - ts.jbig);
+    jbig = (int32_t)ts.jbig;
+    tag = 0;
+  }
   __device__ __forceinline__ uint32_t inc(int32_t j) const {
-    atomicMax(&w[j], tagw);
-    Word old = atomicAdd(&w[j], (Word)1);
-    return (uint32_t)(old & CMASK);
+    if (!BIG || j < jbig) {
+      atomicMax(&w[j], tag << 16);
+      return atomicAdd(&w[j], 1u) & 0xffffu;
+    }
+    unsigned long long* p = &wb[j - jbig];
+    atomicMax(p, (unsigned long long)tag << 32);
+    return (uint32_t)atomicAdd(p, 1ull);
   }
   __device__ __forceinline__ void add(int32_t j) const {    // the same without the old value
-    atomicMax(&w[j], tagw);
-    atomicAdd(&w[j], (Word)1);
+    if (!BIG || j < jbig) {
+      atomicMax(&w[j], tag << 16);
+      atomicAdd(&w[j], 1u);
+    } else {
+      unsigned long long* p = &wb[j - jbig];
+      atomicMax(p, (unsigned long long)tag << 32);
+      atomicAdd(p, 1ull);
+    }
   }
   __device__ __forceinline__ uint32_t get(int32_t j) const {
-    Word v = w[j];
-    return (v & ~CMASK) == tagw ? (uint32_t)(v & CMASK) : 0u;
+    if (!BIG || j < jbig) {
+      uint32_t v = w[j];
+      return (v >> 16) == tag ? (v & 0xffffu) : 0u;
+    }
+    unsigned long long v = wb[j - jbig];
+    return (uint32_t)(v >> 32) == tag ? (uint32_t)v : 0u;
+  }
+  // next item: a new tag, or zeroed counters once the tags are used up (all
+  // threads of the CTA call it; returns true when it zeroed, and a barrier
+  // must then publish the zeros before the next increment)
+  __device__ __forceinline__ bool next(int64_t n) {
+    if (++tag <= TAG_MAX) return false;
+    for (int64_t t = threadIdx.x; t < jbig; t += blockDim.x) w[t] = 0;
+    if (BIG)
+      for (int64_t t = threadIdx.x; t < n - jbig; t += blockDim.x) wb[t] = 0;
+    tag = 1;
+    return true;
   }
 };
 
 
-template <typename Word>
-__global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo, int64_t item_hi, SweepScratch ss,
-                        TriLists tl3, const uint32_t* T, AccSet acc) {
+template <bool BIG>
+__global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo,
+                                                  int64_t item_hi, TagScratch ts, TriLists tl3, const uint32_t* T,
+                                                  AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  TaggedCounters<Word> w{(Word*)ss.cnt + (int64_t)blockIdx.x * ss.n, (Word)0};
+  TaggedCounters<BIG> w(ts);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ids[2] = {ACC_N13, ACC_N17};
   LocalAcc<2> la;
   la.zero();
-  uint64_t tag = 0;                             // items this CTA has taken (the same in every thread)
   while (true) {
     int64_t it = next_item(qctr, item_hi - item_lo, &sh_item);
     if (it < 0) break;
     int64_t i = g.n - 1 - (item_lo + it);
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
     if (e0 - b0 < 2) continue;
-    if (++tag > TaggedCounters<Word>::TAG_MAX) {  // tags used up: zero the counters, start over
-      for (int64_t t = threadIdx.x; t < ss.n; t += blockDim.x) w.w[t] = 0;
-      __syncthreads();
-      tag = 1;
-    }
-    w.tagw = (Word)tag << TaggedCounters<Word>::TB;
+    if (w.next(ts.n)) __syncthreads();
     u128 n13 = 0, n17 = 0;
     // The warp's lists are fetched 32 at a time (lane k holds the k-th), and
     // each lane keeps PAIR_ILP independent loads and counter operations in
@@ -1021,12 +1054,12 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
 // The paths whose own a or b is counted by w' are the directed tailed
 // triangles, subtracted through ACC_N8Z (pass A).
 // ============================================================================
-template <typename Word>
-__global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long long* qctr, SweepScratch ss,
-                                                   AccSet acc) {
+template <bool BIG>
+__global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long long* qctr, TagScratch ts,
+                                                   SweepScratch ss, AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  TaggedCounters<Word> wp{(Word*)ss.cnt + (int64_t)blockIdx.x * ss.n, (Word)0};   // w'(i, .)
+  TaggedCounters<BIG> wp(ts);                                                         // w'(i, .)
   uint32_t* p2 = ss.cnt2 + (int64_t)blockIdx.x * ss.n;                            // P2(i, .), with a list
   int32_t* tl2 = ss.touched2 + (int64_t)blockIdx.x * ss.n;
   unsigned* nt = ss.ntouched + 2 * blockIdx.x;
@@ -1034,18 +1067,13 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
   const int ids[1] = {ACC_N8M};
   LocalAcc<1> la;
   la.zero();
-  uint32_t tag = 0;                             // items this CTA has taken (the same in every thread)
   while (true) {
     int64_t it = next_item(qctr, g.n, &sh_item);
     if (it < 0) break;
     int64_t i = g.n - 1 - it;
     int64_t b0 = g.R[i], o = g.op[i], e0 = g.R[i + 1];
     if (o == b0) continue;                      // needs an in-neighbour a
-    if (++tag > TaggedCounters<Word>::TAG_MAX) {   // tags used up: zero the counters, start over
-      for (int64_t t = threadIdx.x; t < ss.n; t += blockDim.x) wp.w[t] = 0;
-      tag = 1;
-    }
-    wp.tagw = (Word)tag << TaggedCounters<Word>::TB;
+    wp.next(ts.n);
     if (threadIdx.x == 0) nt[1] = 0;
     __syncthreads();
     // w'(i, .): c < i -> every j in N(c); c > i -> j in N+(c).  Lists are
@@ -1671,16 +1699,26 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
   int64_t maxdeg = n > 0 ? hR[n] - hR[n - 1] : 0;   // the highest rank has the largest degree
-  // pair and 5-cycle sweeps: tagged counters, 32-bit words when no count
-  // (W(i,j) or w'(i,j), both at most a degree) can reach 2^16
-  const bool pair_narrow = maxdeg < 65536;
-  size_t swB = (pair_narrow ? sizeof(uint32_t) : sizeof(unsigned long long)) * (size_t)n * grid_sweep + 16;
-  ESC_TRY(b_cntB.alloc(swB));
-  ESC_TRY(b_cntC.alloc(swB));
-  cudaMemsetAsync(b_cntB.p, 0, swB, s);
-  cudaMemsetAsync(b_cntC.p, 0, swB, s);
-  SweepScratch ssB{b_cntB.as<uint32_t>(), nullptr, nullptr, nullptr, nullptr, n};
-  SweepScratch ssC{b_cntC.as<uint32_t>(), nullptr, b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(), b_ntC.as<unsigned>(), n};
+  // pair and 5-cycle sweeps: tagged counters, 32-bit words below the first
+  // rank of degree >= 2^16, 64-bit words from there on
+  int64_t jbig = n;
+  {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] >= 65536) hi = mid; else lo = mid + 1; }
+    jbig = lo;
+  }
+  size_t sw32 = sizeof(uint32_t) * (size_t)jbig * grid_sweep + 16;
+  size_t sw64 = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_sweep + 16;
+  DevBuf b_bigB, b_bigC;
+  ESC_TRY(b_cntB.alloc(sw32)); ESC_TRY(b_bigB.alloc(sw64));
+  ESC_TRY(b_cntC.alloc(sw32)); ESC_TRY(b_bigC.alloc(sw64));
+  cudaMemsetAsync(b_cntB.p, 0, sw32, s);
+  cudaMemsetAsync(b_cntC.p, 0, sw32, s);
+  cudaMemsetAsync(b_bigB.p, 0, sw64, s);
+  cudaMemsetAsync(b_bigC.p, 0, sw64, s);
+  TagScratch tsB{b_cntB.as<uint32_t>(), b_bigB.as<unsigned long long>(), jbig, n};
+  TagScratch tsC{b_cntC.as<uint32_t>(), b_bigC.as<unsigned long long>(), jbig, n};
+  SweepScratch ssC{nullptr, nullptr, b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(), b_ntC.as<unsigned>(), n};
   const int hcap_l = 8192;
   int64_t ghash_cap = pow2_at_least((int)std::max<int64_t>(2 * maxdeg, 2));
   if (2 * maxdeg <= hcap_l) ghash_cap = 2;
@@ -1757,11 +1795,10 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can);
     // whole warps only: the kernel's reductions shuffle across full warps
     int pthreads = std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
-    if (pair_narrow)
-      (k_pairs<uint32_t><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs), note_launch());
+    if (jbig < n)
+      (k_pairs<true><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
     else
-      (k_pairs<unsigned long long><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, ssB, tl3, T, accs),
-       note_launch());
+      (k_pairs<false><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
   }
   mark(5, 1, s);
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)
@@ -1791,10 +1828,10 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // 5-cycles (Thm 13)
   mark(7, 0, s4);
   if (n > 0) {
-    if (pair_narrow)
-      (k_cycles5<uint32_t><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, ssC, accs), note_launch());
+    if (jbig < n)
+      (k_cycles5<true><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs), note_launch());
     else
-      (k_cycles5<unsigned long long><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, ssC, accs), note_launch());
+      (k_cycles5<false><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs), note_launch());
   }
   mark(7, 1, s4);
   ESC_TRY(ss_all.join_into(s));

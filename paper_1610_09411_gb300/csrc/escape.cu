@@ -15,7 +15,7 @@ struct escape_graph {
   int64_t* d_rp = nullptr;     // input CSR, original ids
   int32_t* d_col = nullptr;
   int device = 0, sms = 1;
-  int keep_pe = 0, cta_per_sm = 2, serial = 0;
+  int keep_pe = 0, cta_per_sm = 2, serial = -1;   // serial: 1 on, 0 off, -1 by graph size
   bool has_pe = false;
   esc::PerElement pe;
   esc::Oriented ori;
@@ -255,7 +255,9 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   cfg.sms = g->sms;
   cfg.cta_per_sm = g->cta_per_sm;
   cfg.keep_per_element = keep;
-  cfg.serial_phases = g->serial != 0;
+  // automatic: one phase after another once the graph is large enough that
+  // every sweep fills the GPU alone (overlapping them then only adds contention)
+  cfg.serial_phases = g->serial > 0 || (g->serial < 0 && nnz >= ((int64_t)1 << 24));
   cfg.phase_events = nev ? evs : nullptr;
   cfg.num_phase_events = nev;
   e = esc::run_census(d_rp, d_col, n, nnz, nullptr, 0, cfg, d_out, d_status, keep ? pe : nullptr,
@@ -394,7 +396,7 @@ escape_status escape_set_options(escape_graph* g, int keep_per_element, int cta_
   if (!g || cta_per_sm < 0 || cta_per_sm > 8) return ESCAPE_EINVAL;
   g->keep_pe = keep_per_element ? 1 : 0;
   g->cta_per_sm = cta_per_sm ? cta_per_sm : 2;
-  g->serial = serial_phases ? 1 : 0;
+  g->serial = serial_phases < 0 ? -1 : (serial_phases ? 1 : 0);
   return ESCAPE_OK;
 }
 

@@ -145,9 +145,10 @@ def escape_graph_info(h):
     return n.value, m.value
 
 
-def escape_set_options(h, keep_per_element: bool = False, cta_per_sm: int = 0, serial_phases: bool = False):
-    _check(LIB.escape_set_options(h, int(bool(keep_per_element)), int(cta_per_sm), int(bool(serial_phases))),
-           "escape_set_options")
+def escape_set_options(h, keep_per_element: bool = False, cta_per_sm: int = 0, serial_phases=None):
+    """serial_phases: True / False, or None for the size-based default."""
+    sp = -1 if serial_phases is None else int(bool(serial_phases))
+    _check(LIB.escape_set_options(h, int(bool(keep_per_element)), int(cta_per_sm), sp), "escape_set_options")
 
 
 def escape_census5(h, stream=None) -> dict:

@@ -5,7 +5,7 @@ from the CPU oracle.  Each file records a SHA-256 of the generated CSR so a
 test can tell whether the graph it regenerates is the one the values were
 computed for (and recompute them live if not).
 
-    python tests/golden/make_golden.py chung_lu er500
+    python tests/golden/make_golden.py chung_lu er500 two_hubs
 """
 import json
 import os
@@ -24,6 +24,7 @@ from gpu_util import graph_hash  # noqa: E402
 WORKLOADS = {
     "chung_lu": lambda: gg.config_chung_lu(1),
     "er500": lambda: gg.config_er500(0),
+    "two_hubs": lambda: gg.two_hubs(),
 }
 
 

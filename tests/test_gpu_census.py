@@ -113,6 +113,20 @@ def test_chung_lu_workload():
     assert_same_census(got, want)
 
 
+def test_two_hubs_wide_counts():
+    """Two hubs of degree > 2^16 with > 2^16 common neighbours: the pair and
+    5-cycle counts at the hubs leave 16 bits (stored oracle result)."""
+    from gpu_util import graph_hash
+    g = gg.two_hubs()
+    got = gpu_census(g, device=True)
+    gold = _golden("two_hubs")
+    if gold is not None and gold["sha256"] == graph_hash(g):
+        want = {k: [int(x) for x in gold[k]] for k in ("c3", "c4", "c5", "n3", "n4", "n5")}
+    else:
+        want = oracle.census(g)
+    assert_same_census(got, want)
+
+
 def test_serial_and_concurrent_phases_agree():
     from paper_1610_09411_gb300 import escape as esc
     g = gg.chung_lu(20000, 2.1, 10, 2000, 8)

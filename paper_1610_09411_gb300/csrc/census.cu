@@ -1000,17 +1000,25 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c0, const int64_t* item_off, u
 // per-CTA global region.
 static constexpr int WHEEL_CHUNK = 64;
 
+// Counters are tagged with the u they count for, (tag << 16) | count in the
+// 32-bit shared-memory words and (tag << 32) | count in the 64-bit global ones
+// (counts there can pass 2^16); before each increment an atomicMax with the
+// current tag turns an older entry into a zero count, so no clearing pass
+// walks the lists a second time.  A CTA's tags grow with the u's it takes.
 __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, int64_t nitems,
-                             unsigned long long* qctr, TriLists tl3, const uint32_t* T, uint32_t* gscr,
+                             unsigned long long* qctr, TriLists tl3, const uint32_t* T, unsigned long long* gscr,
                              int64_t gscr_stride, int smem_cap, AccSet acc) {
   extern __shared__ uint32_t sscr[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ids[1] = {ACC_N18};
   LocalAcc<1> la;
   la.zero();
-  bool zeroed_smem = false;
+  unsigned long long* g64 = gscr + (int64_t)blockIdx.x * gscr_stride;
+  for (int i = threadIdx.x; i < smem_cap; i += blockDim.x) sscr[i] = 0;
+  __syncthreads();
+  uint32_t tag = 0;                             // the same in every thread of the CTA
   while (true) {
     int64_t it = next_item(qctr, nitems, &sh_item);
     if (it < 0) break;
@@ -1023,23 +1031,33 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
     int d = (int)(g.R[c + 1] - base);
     int u0 = (int)(it - item_off[lo]) * WHEEL_CHUNK;
     int u1 = min(d, u0 + WHEEL_CHUNK);
-    uint32_t* scr = d <= smem_cap ? sscr : gscr + (int64_t)blockIdx.x * gscr_stride;
-    if (d <= smem_cap && !zeroed_smem) {
-      for (int i = threadIdx.x; i < smem_cap; i += blockDim.x) sscr[i] = 0;
-      zeroed_smem = true;
-      __syncthreads();
-    }
+    const bool in_smem = d <= smem_cap;
     for (int pu = u0; pu < u1; ++pu) {
       uint32_t lenu = T[base + pu];
       if (lenu < 2) continue;
+      if (++tag > 0xffffu) {                    // tags used up: zero both counter sets, start over
+        for (int i = threadIdx.x; i < smem_cap; i += blockDim.x) sscr[i] = 0;
+        for (int64_t i = threadIdx.x; i < gscr_stride; i += blockDim.x) g64[i] = 0;
+        __syncthreads();
+        tag = 1;
+      }
       const int32_t* Lu = tl3.P + tl3.offp[base + pu];
       unsigned long long part = 0;
-      wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw,
-                  [&](int32_t pv) { part += atomicAdd(&scr[pv], 1u); });
+      if (in_smem) {
+        const uint32_t t16 = tag << 16;
+        wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw, [&](int32_t pv) {
+          atomicMax(&sscr[pv], t16);
+          part += atomicAdd(&sscr[pv], 1u) & 0xffffu;
+        });
+      } else {
+        const unsigned long long t32 = (unsigned long long)tag << 32;
+        wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw, [&](int32_t pv) {
+          atomicMax(&g64[pv], t32);
+          part += (uint32_t)atomicAdd(&g64[pv], 1ull);
+        });
+      }
       la.v[0] += part;
-      __syncthreads();
-      wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw, [&](int32_t pv) { scr[pv] = 0; });
-      __syncthreads();
+      __syncthreads();                          // the next u's tag must not meet this u's increments
     }
     block_item_flush(la, ids, acc, c, sh);
   }
@@ -1748,8 +1766,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     nitems_w = item_off[n - c0];
     ESC_TRY(b_io.alloc(sizeof(int64_t) * (n - c0 + 1)));
     cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
-    ESC_TRY(b_gs.alloc(sizeof(uint32_t) * (size_t)gstride * 2 * sms + 16));
-    cudaMemsetAsync(b_gs.p, 0, sizeof(uint32_t) * (size_t)gstride * 2 * sms + 16, s);
+    ESC_TRY(b_gs.alloc(sizeof(unsigned long long) * (size_t)gstride * 2 * sms + 16));
+    cudaMemsetAsync(b_gs.p, 0, sizeof(unsigned long long) * (size_t)gstride * 2 * sms + 16, s);
     ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
   }
   DevBuf b_wo;                                 // warp wheel items: offsets over centres c0-1 .. 0
@@ -1781,7 +1799,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(6, 0, s3);
   if (c0 < n)
     (k_wheels_cta<<<2 * sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
-                                            b_gs.as<uint32_t>(), gstride, smem_cap, accs), note_launch());
+                                            b_gs.as<unsigned long long>(), gstride, smem_cap, accs), note_launch());
   if (c0 > 0) {
     int per_sm = 1;
     ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wheels_warp, 256, 0));

@@ -88,7 +88,10 @@ escape_status escape_graph_info(const escape_graph* g, int64_t* n, int64_t* m);
  * 5-vertex patterns; Thm 3: disconnected ones; App. B: induced counts),
  * together with the 3- and 4-vertex census (Thm 1).
  *   out      host memory; written only on success.
- * Device work space is allocated for the call and freed before it returns.
+ * Device work space is allocated for the call and released before it returns;
+ * released buffers (up to 8 GiB per device) are kept for later calls instead
+ * of being freed, and the whole cache is freed whenever an allocation of a
+ * later call would otherwise fail.
  * Graphs with n < 5, no edges, or no triangles are valid.
  */
 escape_status escape_census5(escape_graph* g, escape_census* out, void* stream);

@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <initializer_list>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <vector>
 
@@ -1479,10 +1481,108 @@ static cudaError_t check_status(unsigned* d_status, cudaStream_t s, unsigned* h)
   return e;
 }
 
+// ---------------------------------------------------------------- buffers
+// Device buffers of one census.  Repeated censuses would otherwise pay dozens
+// of cudaMalloc / cudaFree calls each (cudaFree synchronises the device), so
+// buffers released by a census are kept in a per-device cache, up to
+// kCacheCap bytes, and handed to later ones: a request takes the smallest
+// cached buffer that is large enough and at most twice the size.  Release
+// happens only after the census's stream has drained (CacheScope), so a
+// buffer never changes hands while kernels may still use it.  If cudaMalloc
+// fails, the cache is emptied and the allocation tried once more.
+static constexpr size_t kCacheCap = (size_t)8 << 30;
+
+class BufCache {
+ public:
+  void* get(int dev, size_t b, size_t* got) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto& m = free_[dev & 63];
+    auto it = m.lower_bound(b);
+    if (it == m.end() || it->first > 2 * b) return nullptr;
+    void* p = it->second;
+    *got = it->first;
+    bytes_[dev & 63] -= it->first;
+    m.erase(it);
+    return p;
+  }
+  void put(int dev, void* p, size_t b) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (bytes_[dev & 63] + b <= kCacheCap) {
+        free_[dev & 63].emplace(b, p);
+        bytes_[dev & 63] += b;
+        return;
+      }
+    }
+    cudaFree(p);
+  }
+  void clear(int dev) {
+    std::multimap<size_t, void*> m;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      m.swap(free_[dev & 63]);
+      bytes_[dev & 63] = 0;
+    }
+    for (auto& kv : m) cudaFree(kv.second);
+  }
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, void*> free_[64];
+  size_t bytes_[64] = {};
+};
+static BufCache g_cache;
+
+// Buffers released inside a scope wait until the scope ends, and the scope
+// ends by draining its stream.
+struct CacheScope;
+static thread_local CacheScope* t_scope = nullptr;
+struct CacheScope {
+  cudaStream_t s;
+  int dev = 0;
+  CacheScope* prev;
+  std::vector<std::pair<void*, size_t>> pending;
+  explicit CacheScope(cudaStream_t st) : s(st), prev(t_scope) {
+    cudaGetDevice(&dev);
+    t_scope = this;
+  }
+  ~CacheScope() {
+    cudaStreamSynchronize(s);
+    for (auto& pb : pending) g_cache.put(dev, pb.first, pb.second);
+    t_scope = prev;
+  }
+};
+
 struct DevBuf {
   void* p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
-  cudaError_t alloc(size_t b) { return cudaMalloc(&p, b > 0 ? b : 16); }
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (!p) return;
+    if (t_scope) t_scope->pending.emplace_back(p, bytes);
+    else cudaFree(p);
+  }
+  cudaError_t alloc(size_t b) {
+    b = ((b > 0 ? b : 16) + 255) & ~(size_t)255;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    size_t got = 0;
+    if ((p = g_cache.get(dev, b, &got)) != nullptr) {
+      bytes = got;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      g_cache.clear(dev);
+      e = cudaMalloc(&p, b);
+    }
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+  }
   template <class T> T* as() { return (T*)p; }
 };
 
@@ -1537,6 +1637,7 @@ struct StreamSet {
 cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, void* /*scratch*/,
                        size_t /*scratch_bytes*/, const CensusConfig& cfg, unsigned long long* d_out,
                        unsigned* d_status, PerElement* pe_out, Oriented* or_out, cudaStream_t s) {
+  CacheScope cache_scope(s);                    // destroyed last: the buffers below return after the stream drains
   const int sms = cfg.sms > 0 ? cfg.sms : 1;
   // phase k is timed by events 2k (begin) and 2k+1 (end) on the stream that runs it
   auto mark = [&](int k, int end, cudaStream_t st) {

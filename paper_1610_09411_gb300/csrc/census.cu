@@ -1781,7 +1781,15 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
                   sizeof(uint32_t) * dmax;
   if (smem_b + 1024 > (size_t)smem_optin) return cudaErrorInvalidConfiguration;   // d+ beyond the bit matrix
   ESC_TRY(cudaFuncSetAttribute(k_clique_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-  const int blocks_b = sms;   // one CTA per SM (large shared memory)
+  // as many 256-thread CTAs per SM as registers and the bit matrix allow;
+  // one 512-thread CTA per SM when fewer than two fit (large bit matrices)
+  int clq_threads = 256, clq_per_sm = 1;
+  ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&clq_per_sm, k_clique_large, clq_threads, smem_b));
+  if (clq_per_sm < 2) {
+    clq_threads = 512;
+    clq_per_sm = 1;
+  }
+  const int blocks_b = sms * std::min(clq_per_sm, 4);
   unsigned long long dwords = dims[0] > 0 ? dims[0] : 1;
   ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
   CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
@@ -1923,7 +1931,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)
   mark(2, 0, s1);
   if (nitems_b > 0)
-    (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), 512, smem_b, s1>>>(
+    (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), clq_threads, smem_b, s1>>>(
         g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, dmax, d_status), note_launch());
   if (nwsmall > 0) {
     int per_sm = 1;

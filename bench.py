@@ -323,12 +323,14 @@ def run_serve_bench(args):
         for mode, kw in (("continuous_batching", dict(workers=3)),
                          ("one_at_a_time", dict(workers=1, max_batch=1))):
             srv = CensusServer(budget_bytes=120e9, **kw)
-            t0 = time.perf_counter()
-            futs = replay(srv, graphs, arr)
-            for f in futs:
-                f.result()
-            span = time.perf_counter() - t0
-            srv.close()
+            try:
+                t0 = time.perf_counter()
+                futs = replay(srv, graphs, arr)
+                for f in futs:
+                    f.result()
+                span = time.perf_counter() - t0
+            finally:
+                srv.close()
             st = srv.latency_stats()
             st["edges_per_s"] = edges / span
             st["makespan_s"] = span

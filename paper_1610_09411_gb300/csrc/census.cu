@@ -1634,11 +1634,28 @@ struct StreamSet {
   }
 };
 
+// Lets kernel k use all of the device's opt-in shared memory (less its static
+// shared memory) as dynamic shared memory.  Every call sets the same value, so
+// censuses running on other host threads never lower the limit between this
+// thread's setting and its launch.
+static cudaError_t allow_max_smem(const void* k, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, void* /*scratch*/,
                        size_t /*scratch_bytes*/, const CensusConfig& cfg, unsigned long long* d_out,
                        unsigned* d_status, PerElement* pe_out, Oriented* or_out, cudaStream_t s) {
   CacheScope cache_scope(s);                    // destroyed last: the buffers below return after the stream drains
   const int sms = cfg.sms > 0 ? cfg.sms : 1;
+  int smem_optin = 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
   // phase k is timed by events 2k (begin) and 2k+1 (end) on the stream that runs it
   auto mark = [&](int k, int end, cudaStream_t st) {
     int i = 2 * k + end;
@@ -1749,7 +1766,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (nsmall > 0)
     (k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, accs), note_launch());
   if (nlarge > 0) {
-    if (smem_a > 48 * 1024) ESC_TRY(cudaFuncSetAttribute(k_tri_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+    if (smem_a > 48 * 1024) ESC_TRY(allow_max_smem((const void*)k_tri_large, smem_optin));
     (k_tri_large<<<(unsigned)std::min<int64_t>(grid_sweep, nlarge), 512, smem_a, s>>>(
         g, b_large.as<int32_t>(), nlarge, ctr + 0, T, accs, hcap_a), note_launch());
   }
@@ -1763,8 +1780,6 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // allocated here, so no branch below waits on the host
   int dev = 0;
   cudaGetDevice(&dev);
-  int smem_optin = 0;
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // pass B inputs
   // CTA items: every large out-neighbourhood, then the small ones with many
   // in-neighbours; the other small ones go to the warp kernel
@@ -1780,7 +1795,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   size_t smem_b = sizeof(uint64_t) * ((size_t)dmax * W_cap + dmax) + sizeof(int32_t) * (2 * (size_t)hcap_b) +
                   sizeof(uint32_t) * dmax;
   if (smem_b + 1024 > (size_t)smem_optin) return cudaErrorInvalidConfiguration;   // d+ beyond the bit matrix
-  ESC_TRY(cudaFuncSetAttribute(k_clique_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  ESC_TRY(allow_max_smem((const void*)k_clique_large, smem_optin));
   // as many 256-thread CTAs per SM as registers and the bit matrix allow;
   // one 512-thread CTA per SM when fewer than two fit (large bit matrices)
   int clq_threads = 256, clq_per_sm = 1;
@@ -1851,7 +1866,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (2 * maxdeg <= hcap_l) ghash_cap = 2;
   ESC_TRY(b_gh.alloc(sizeof(int32_t) * 2 * (size_t)ghash_cap * grid_sweep + 16));
   size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
-  ESC_TRY(cudaFuncSetAttribute(k_tri_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
+  ESC_TRY(allow_max_smem((const void*)k_tri_lists, smem_optin));
   TriLists tl3{off, b_U.as<int32_t>(), offp, b_P.as<int32_t>()};
 
   // wheel work items: ranks are in degree order, so the large centres are a suffix
@@ -1877,7 +1892,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
     ESC_TRY(b_gs.alloc(sizeof(unsigned long long) * (size_t)gstride * 2 * sms + 16));
     cudaMemsetAsync(b_gs.p, 0, sizeof(unsigned long long) * (size_t)gstride * 2 * sms + 16, s);
-    ESC_TRY(cudaFuncSetAttribute(k_wheels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
+    ESC_TRY(allow_max_smem((const void*)k_wheels_cta, smem_optin));
   }
   DevBuf b_wo;                                 // warp wheel items: offsets over centres c0-1 .. 0
   if (c0 > 0) {

@@ -127,6 +127,45 @@ def test_two_hubs_wide_counts():
     assert_same_census(got, want)
 
 
+def test_censuses_on_concurrent_host_threads():
+    """Censuses issued at the same time from several host threads, each on its
+    own stream, over graphs whose kernels need different shared-memory sizes
+    (as a serving loop with several workers does), give each graph's result
+    alone."""
+    import threading
+    import torch
+    from paper_1610_09411_gb300 import escape as esc
+    graphs = [gg.complete(40), gg.complete(90), gg.chung_lu(6000, 2.1, 10, 1500, 3),
+              gg.barabasi_albert(4000, 6, 2), gg.disjoint_union([gg.star(3000), gg.complete(70)])]
+    want = [gpu_census(g) for g in graphs]
+    errors, got = [], {}
+
+    def worker(k):
+        try:
+            st = torch.cuda.Stream()
+            for rnd in range(3):
+                for t, g in enumerate(graphs):
+                    if (t + k + rnd) % 2:
+                        continue
+                    h = esc.escape_load_csr(g.n, g.row_ptr, g.col, stream=st.cuda_stream)
+                    try:
+                        got[(k, rnd, t)] = esc.escape_census5(h, stream=st.cuda_stream)
+                    finally:
+                        esc.escape_free(h)
+        except Exception as e:      # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(3)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    assert got
+    for (k, rnd, t), r in got.items():
+        assert_same_census(r, want[t])
+
+
 def test_serial_and_concurrent_phases_agree():
     from paper_1610_09411_gb300 import escape as esc
     g = gg.chung_lu(20000, 2.1, 10, 2000, 8)

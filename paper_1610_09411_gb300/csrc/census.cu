@@ -564,10 +564,17 @@ __global__ void __launch_bounds__(CLQ_WARPS * 32) k_clique_warp(DevGraph g, cons
 // (i,k), (k,j) and vertex k; every j adds C(w,2) to vertices i and j.
 // CTA per i, dense per-CTA counters over j with a touched list.
 // ============================================================================
-#ifndef ESC_PAIR_ILP
-#define ESC_PAIR_ILP 8
+#ifndef ESC_SWEEP_ILP
+#define ESC_SWEEP_ILP 8
 #endif
-static constexpr int PAIR_ILP = ESC_PAIR_ILP;   // independent accesses in flight per lane (sweeps)
+static constexpr int SWEEP_ILP = ESC_SWEEP_ILP;   // independent accesses in flight per lane (4- and 5-cycles)
+// The pair sweep runs three 512-thread CTAs per SM (40 registers a thread),
+// which leaves room for fewer accesses in flight per lane.
+#ifndef ESC_PAIR_ILP
+#define ESC_PAIR_ILP 4
+#endif
+static constexpr int PAIR_ILP = ESC_PAIR_ILP;
+static constexpr int PAIR_CTAS_PER_SM = 3;
 
 struct SweepScratch {
   uint32_t* cnt;       // per CTA: n counters (kept zero between items)
@@ -596,7 +603,7 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
     if (threadIdx.x == 0) *nt = 0;
     __syncthreads();
     // pass 1: wedge counts.  The lists N(k) below i are fetched 32 per warp
-    // (lane l the l-th), PAIR_ILP entries in flight per lane.
+    // (lane l the l-th), SWEEP_ILP entries in flight per lane.
     for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
       int64_t p = pbase + (int64_t)lane * nw;
       int64_t kb_l = 0, ke_l = 0;
@@ -607,15 +614,15 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
       for (int kk = 0; kk < kmax; ++kk) {
         int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
-        for (int64_t q = kb + lane; q < ke; q += 32 * PAIR_ILP) {
-          int32_t jj[PAIR_ILP];
-          uint32_t oo[PAIR_ILP];
+        for (int64_t q = kb + lane; q < ke; q += 32 * SWEEP_ILP) {
+          int32_t jj[SWEEP_ILP];
+          uint32_t oo[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? atomicAdd(&w[jj[u]], 1u) : 1u;
+          for (int u = 0; u < SWEEP_ILP; ++u) oo[u] = jj[u] >= 0 ? atomicAdd(&w[jj[u]], 1u) : 1u;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) warp_append(tl, nt, oo[u] == 0, jj[u]);
+          for (int u = 0; u < SWEEP_ILP; ++u) warp_append(tl, nt, oo[u] == 0, jj[u]);
         }
       }
     }
@@ -647,12 +654,12 @@ __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss,
       for (int kk = 0; kk < kmax; ++kk) {
         int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
         unsigned long long sk = 0;
-        for (int64_t q = kb + lane; q < ke; q += 32 * PAIR_ILP) {
-          int32_t jj[PAIR_ILP];
+        for (int64_t q = kb + lane; q < ke; q += 32 * SWEEP_ILP) {
+          int32_t jj[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) {
+          for (int u = 0; u < SWEEP_ILP; ++u) {
             if (jj[u] < 0) continue;
             unsigned long long c = w[jj[u]] - 1;
             if (c) { atomicAdd(&C4raw[q + 32 * u], c); sk += c; }
@@ -760,7 +767,7 @@ struct TaggedCounters {
 
 
 template <bool BIG>
-__global__ void __launch_bounds__(512, 2) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo,
+__global__ void __launch_bounds__(512, PAIR_CTAS_PER_SM) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo,
                                                   int64_t item_hi, TagScratch ts, TriLists tl3, const uint32_t* T,
                                                   AccSet acc) {
   __shared__ u128 sh[32];
@@ -1097,7 +1104,7 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
     if (threadIdx.x == 0) nt[1] = 0;
     __syncthreads();
     // w'(i, .): c < i -> every j in N(c); c > i -> j in N+(c).  Lists are
-    // fetched 32 per warp (lane k the k-th), PAIR_ILP entries in flight per lane.
+    // fetched 32 per warp (lane k the k-th), SWEEP_ILP entries in flight per lane.
     for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
       int64_t p = pbase + (int64_t)lane * nw;
       int64_t cb_l = 0, ce_l = 0;
@@ -1109,12 +1116,12 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
       int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
       for (int k = 0; k < kmax; ++k) {
         int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
-        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
-          int32_t jj[PAIR_ILP];
+        for (int64_t q = cb + lane; q < ce; q += 32 * SWEEP_ILP) {
+          int32_t jj[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u)
+          for (int u = 0; u < SWEEP_ILP; ++u)
             if (jj[u] != i) wp.add(jj[u]);
         }
       }
@@ -1131,15 +1138,15 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
       int kmax = (int)min((int64_t)32, (o - pbase + nw - 1) / nw);
       for (int k = 0; k < kmax; ++k) {
         int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
-        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
-          int32_t bb[PAIR_ILP];
-          uint32_t oo[PAIR_ILP];
+        for (int64_t q = cb + lane; q < ce; q += 32 * SWEEP_ILP) {
+          int32_t bb[SWEEP_ILP];
+          uint32_t oo[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) bb[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
+          for (int u = 0; u < SWEEP_ILP; ++u) bb[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) oo[u] = bb[u] != i ? atomicAdd(&p2[bb[u]], 1u) : 1u;
+          for (int u = 0; u < SWEEP_ILP; ++u) oo[u] = bb[u] != i ? atomicAdd(&p2[bb[u]], 1u) : 1u;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) warp_append(tl2, &nt[1], oo[u] == 0, bb[u]);
+          for (int u = 0; u < SWEEP_ILP; ++u) warp_append(tl2, &nt[1], oo[u] == 0, bb[u]);
         }
       }
     }
@@ -1162,12 +1169,12 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
         int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
         uint32_t pk = __shfl_sync(0xffffffffu, pk_l, k);
         unsigned long long s_ = 0;
-        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
-          int32_t jj[PAIR_ILP];
+        for (int64_t q = cb + lane; q < ce; q += 32 * SWEEP_ILP) {
+          int32_t jj[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : -1;
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : -1;
 #pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u)
+          for (int u = 0; u < SWEEP_ILP; ++u)
             if (jj[u] >= 0) s_ += wp.get(jj[u]);
         }
         la.v[0] += (u128)s_ * pk;
@@ -1849,14 +1856,19 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] >= 65536) hi = mid; else lo = mid + 1; }
     jbig = lo;
   }
+  // the pair sweep: PAIR_CTAS_PER_SM persistent CTAs per SM unless the
+  // caller asked for a different count
+  const int grid_pairs = sms * (cfg.cta_per_sm == 2 ? PAIR_CTAS_PER_SM : std::max(1, cfg.cta_per_sm));
   size_t sw32 = sizeof(uint32_t) * (size_t)jbig * grid_sweep + 16;
   size_t sw64 = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_sweep + 16;
+  size_t sw32p = sizeof(uint32_t) * (size_t)jbig * grid_pairs + 16;
+  size_t sw64p = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_pairs + 16;
   DevBuf b_bigB, b_bigC;
-  ESC_TRY(b_cntB.alloc(sw32)); ESC_TRY(b_bigB.alloc(sw64));
+  ESC_TRY(b_cntB.alloc(sw32p)); ESC_TRY(b_bigB.alloc(sw64p));
   ESC_TRY(b_cntC.alloc(sw32)); ESC_TRY(b_bigC.alloc(sw64));
-  cudaMemsetAsync(b_cntB.p, 0, sw32, s);
+  cudaMemsetAsync(b_cntB.p, 0, sw32p, s);
   cudaMemsetAsync(b_cntC.p, 0, sw32, s);
-  cudaMemsetAsync(b_bigB.p, 0, sw64, s);
+  cudaMemsetAsync(b_bigB.p, 0, sw64p, s);
   cudaMemsetAsync(b_bigC.p, 0, sw64, s);
   TagScratch tsB{b_cntB.as<uint32_t>(), b_bigB.as<unsigned long long>(), jbig, n};
   TagScratch tsC{b_cntC.as<uint32_t>(), b_bigC.as<unsigned long long>(), jbig, n};
@@ -1936,11 +1948,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   if (n > 0) {
     // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can);
     // whole warps only: the kernel's reductions shuffle across full warps
-    int pthreads = std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
+    int pthreads = cfg.cta_per_sm == 2 ? 512 : std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
     if (jbig < n)
-      (k_pairs<true><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
+      (k_pairs<true><<<grid_pairs, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
     else
-      (k_pairs<false><<<grid_sweep, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
+      (k_pairs<false><<<grid_pairs, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
   }
   mark(5, 1, s);
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)

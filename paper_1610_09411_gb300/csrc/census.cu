@@ -872,18 +872,6 @@ __global__ void __launch_bounds__(512, PAIR_CTAS_PER_SM) k_pairs(DevGraph g, uns
 // ============================================================================
 static constexpr int WHEEL_WARP_MAX = 1024;     // centres up to this degree: warp items
 
-// Counter tagged with the u it was counted for: (tag << 16) | count.  An entry
-// whose tag differs counts as zero, so nothing has to be cleared between u's.
-__device__ __forceinline__ uint32_t tagged_inc(uint32_t* p, uint32_t tag) {
-  uint32_t old = *(volatile uint32_t*)p, assumed;
-  do {
-    assumed = old;
-    uint32_t nv = ((assumed >> 16) == tag) ? assumed + 1 : ((tag << 16) | 1u);
-    old = atomicCAS(p, assumed, nv);
-  } while (old != assumed);
-  return ((assumed >> 16) == tag) ? (assumed & 0xffffu) : 0u;
-}
-
 // Walks, for one centre c and one position pu, every k in N(c) cap N(u) below
 // u (a prefix of the list of slot c -> u) and every v in N(c) cap N(k) below u
 // (a prefix of the list of slot c -> k), calling visit(pv) once per pair with
@@ -940,9 +928,10 @@ __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t*
 
 // Centres up to WHEEL_WARP_MAX: work items are (centre, block of WHEEL_WBLK
 // positions u), pulled by whole warps from a queue, heaviest centres first.
-// Each warp owns a counter array in shared memory whose entries carry the tag
-// of the u they were counted for; a fresh tag per u makes every older entry
-// count as zero, so nothing is cleared between u's or items.
+// Each warp owns a counter array in shared memory whose entries are
+// (tag << 16) | count for the u they were counted for; before each increment
+// an atomicMax with the current u's tag turns an older entry into a zero
+// count, so nothing is cleared between u's or items.
 static constexpr int WHEEL_WBLK = 32;
 
 // item_cnt[k] = number of items of centre c0 - 1 - k (position k in the queue)
@@ -954,8 +943,9 @@ __global__ void k_wheel_warp_counts(DevGraph g, int64_t c0, int64_t* item_cnt) {
   }
 }
 
-__global__ void k_wheels_warp(DevGraph g, int64_t c0, const int64_t* item_off, unsigned long long* qctr,
-                              TriLists tl3, const uint32_t* T, AccSet acc) {
+__global__ void __launch_bounds__(256, 6) k_wheels_warp(DevGraph g, int64_t c0, const int64_t* item_off,
+                                                        unsigned long long* qctr, TriLists tl3, const uint32_t* T,
+                                                        AccSet acc) {
   __shared__ u128 sh[32];
   __shared__ uint32_t scr_all[8][WHEEL_WARP_MAX];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -995,7 +985,12 @@ __global__ void k_wheels_warp(DevGraph g, int64_t c0, const int64_t* item_off, u
       }
       const int32_t* Lu = tl3.P + tl3.offp[base + pu];
       unsigned long long part = 0;
-      wheel_links(tl3, T, base, Lu, lenu, pu, 0u, 1u, [&](int32_t pv) { part += tagged_inc(&scr[pv], tag); });
+      const uint32_t t16 = tag << 16;
+      wheel_links(tl3, T, base, Lu, lenu, pu, 0u, 1u, [&](int32_t pv) {
+        atomicMax(&scr[pv], t16);               // an older u's entry becomes a zero count of this one
+        part += atomicAdd(&scr[pv], 1u) & 0xffffu;
+      });
+      __syncwarp();                             // this u's increments before the next u's tag
       n18 += part;
     }
     la.v[0] += n18;

@@ -439,7 +439,7 @@ static constexpr int CLQ_WARP_DIN = 512;
 static constexpr int CLQ_WARPS = 8;            // warps per block
 static constexpr int CLQ_ILP = 4;
 
-__global__ void __launch_bounds__(CLQ_WARPS * 32) k_clique_warp(DevGraph g, const int32_t* items, int64_t nitems,
+__global__ void __launch_bounds__(CLQ_WARPS * 32, 4) k_clique_warp(DevGraph g, const int32_t* items, int64_t nitems,
                                                                 unsigned long long* qctr, const uint32_t* T,
                                                                 unsigned long long* K4e, AccSet acc) {
   __shared__ u128 sh[32];

@@ -557,153 +557,12 @@ __global__ void __launch_bounds__(CLQ_WARPS * 32, 4) k_clique_warp(DevGraph g, c
   final_flush(la, ids, acc, sh);
 }
 
-// ============================================================================
-// Thm 5: 4-cycles.  For the highest vertex i and each j < i,
-// w(i,j) = |{k in N(i) cap N(j) : k < i}| (out-wedges and in-out wedges);
-// C4 = sum C(w,2).  Per element: every wedge i - k - j adds w-1 to edges
-// (i,k), (k,j) and vertex k; every j adds C(w,2) to vertices i and j.
-// CTA per i, dense per-CTA counters over j with a touched list.
-// ============================================================================
-#ifndef ESC_SWEEP_ILP
-#define ESC_SWEEP_ILP 8
-#endif
-static constexpr int SWEEP_ILP = ESC_SWEEP_ILP;   // independent accesses in flight per lane (4- and 5-cycles)
-// The pair sweep runs three 512-thread CTAs per SM (40 registers a thread),
-// which leaves room for fewer accesses in flight per lane.
-#ifndef ESC_PAIR_ILP
-#define ESC_PAIR_ILP 4
-#endif
-static constexpr int PAIR_ILP = ESC_PAIR_ILP;
-static constexpr int PAIR_CTAS_PER_SM = 3;
-
-struct SweepScratch {
-  uint32_t* cnt;       // per CTA: n counters (kept zero between items)
-  int32_t* touched;    // per CTA: n entries
-  uint32_t* cnt2;      // second counter array (5-cycles)
-  int32_t* touched2;
-  unsigned* ntouched;  // per CTA: 2 counters
-  int64_t n;
-};
-
-__global__ void k_cycles4(DevGraph g, unsigned long long* qctr, SweepScratch ss, unsigned long long* C4raw,
-                          unsigned long long* C4v, AccSet acc) {
-  __shared__ u128 sh[32];
-  __shared__ int64_t sh_item;
-  uint32_t* w = ss.cnt + (int64_t)blockIdx.x * ss.n;
-  int32_t* tl = ss.touched + (int64_t)blockIdx.x * ss.n;
-  unsigned* nt = ss.ntouched + 2 * blockIdx.x;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  u128 c4sum = 0;
-  while (true) {
-    int64_t it = next_item(qctr, g.n, &sh_item);
-    if (it < 0) break;
-    int64_t i = g.n - 1 - it;
-    int64_t b0 = g.R[i], e0 = g.op[i];
-    if (e0 == b0) continue;           // no lower neighbours
-    if (threadIdx.x == 0) *nt = 0;
-    __syncthreads();
-    // pass 1: wedge counts.  The lists N(k) below i are fetched 32 per warp
-    // (lane l the l-th), SWEEP_ILP entries in flight per lane.
-    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
-      int64_t p = pbase + (int64_t)lane * nw;
-      int64_t kb_l = 0, ke_l = 0;
-      if (p < e0) {
-        kb_l = g.R[g.C[p]];
-        ke_l = g.rev[p];                        // N(k) below i ends at the slot of i
-      }
-      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
-      for (int kk = 0; kk < kmax; ++kk) {
-        int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
-        for (int64_t q = kb + lane; q < ke; q += 32 * SWEEP_ILP) {
-          int32_t jj[SWEEP_ILP];
-          uint32_t oo[SWEEP_ILP];
-#pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
-#pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) oo[u] = jj[u] >= 0 ? atomicAdd(&w[jj[u]], 1u) : 1u;
-#pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) warp_append(tl, nt, oo[u] == 0, jj[u]);
-        }
-      }
-    }
-    __syncthreads();
-    unsigned ntc = *nt;
-    u128 mine = 0;
-    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) {
-      int32_t j = tl[t];
-      u128 c = ch2(w[j]);
-      if (c) { atomicAdd(&C4v[j], (unsigned long long)c); mine += c; }
-    }
-    u128 tot = block_sum_u128(mine, sh);
-    if (threadIdx.x == 0) {
-      if (tot) atomicAdd(&C4v[i], (unsigned long long)tot);
-      if (acc.vg) acc_add(acc_of(acc, i), ACC_C4, tot);
-      else c4sum += tot;
-    }
-    // pass 3: per-edge counts, the lists fetched as in pass 1
-    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
-      int64_t p_l = pbase + (int64_t)lane * nw;
-      int64_t kb_l = 0, ke_l = 0;
-      int32_t k_l = 0;
-      if (p_l < e0) {
-        k_l = g.C[p_l];
-        kb_l = g.R[k_l];
-        ke_l = g.rev[p_l];
-      }
-      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
-      for (int kk = 0; kk < kmax; ++kk) {
-        int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
-        unsigned long long sk = 0;
-        for (int64_t q = kb + lane; q < ke; q += 32 * SWEEP_ILP) {
-          int32_t jj[SWEEP_ILP];
-#pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
-#pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) {
-            if (jj[u] < 0) continue;
-            unsigned long long c = w[jj[u]] - 1;
-            if (c) { atomicAdd(&C4raw[q + 32 * u], c); sk += c; }
-          }
-        }
-        sk = warp_sum_u64(sk);
-        int32_t k = __shfl_sync(0xffffffffu, k_l, kk);
-        if (lane == 0 && sk) {
-          atomicAdd(&C4raw[pbase + (int64_t)kk * nw], sk);
-          atomicAdd(&C4v[k], sk);
-        }
-      }
-    }
-    __syncthreads();
-    for (unsigned t = threadIdx.x; t < ntc; t += blockDim.x) w[tl[t]] = 0;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && !acc.vg) acc_add(acc.base, ACC_C4, c4sum);
-}
-
-// Per-edge common-neighbour lists (built by the triangle-list pass).
-struct TriLists {
-  const int64_t* off;    // per slot: start of the edge's id list (both slots of an edge share it)
-  const int32_t* U;      // sorted common-neighbour ids
-  const int64_t* offp;   // per slot: start of the slot's position list
-  const int32_t* P;      // per slot (u -> v): positions in row u of the common neighbours, ascending
-};
-
-// ============================================================================
-// Thm 11/12: N13 = sum_{j<i} C(W(i,j), 3) and
-// N17 = sum_{j<i} (W(i,j) - 2) cc(i,j), cc = edges inside N(i) cap N(j).
-// W(i,.) from every wedge i - c - j (c in N(i), j in N(c), j < i); C(W,3) is
-// accumulated on the fly as the sum of C(old, 2) over the increments.  The cc
-// term is gathered per diamond: for each triangle {i, x, y} (x < y, y reached
-// through the position list of (x, i), so its slot in row x is direct) and each
-// j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
-// per-edge triangle lists).
-// ============================================================================
-// Counters of the pair and 5-cycle sweeps, tagged with the item they count
+// Counters of the 4-cycle, pair and 5-cycle sweeps, tagged with the item they count
 // for.  Before each increment a fire-and-forget atomicMax with the current tag
 // turns an entry left by an earlier item into a zero count of the current one
 // (a CTA's tags grow with the items it takes), so nothing is cleared between
-// items and no list of touched entries is kept.  Every count at j (W(i,j) or
-// w'(i,j)) is at most d(j), so the ranks below jbig, the first of degree
+// items and no list of touched entries is kept.  Every count at j (w(i,j),
+// W(i,j) or w'(i,j)) is at most d(j), so the ranks below jbig, the first of degree
 // >= 2^16, keep (tag << 16) | count in 32-bit words; the few ranks from jbig on
 // keep (tag << 32) | count in a 64-bit side array.
 struct TagScratch {
@@ -764,6 +623,144 @@ struct TaggedCounters {
     return true;
   }
 };
+
+// ============================================================================
+// Thm 5: 4-cycles.  For the highest vertex i and each j < i,
+// w(i,j) = |{k in N(i) cap N(j) : k < i}| (out-wedges and in-out wedges);
+// C4 = sum C(w,2).  Per element: every wedge i - k - j adds w-1 to edges
+// (i,k), (k,j) and vertex k; every j adds C(w,2) to vertices i and j.
+// CTA per i, dense per-CTA counters over j with a touched list.
+// ============================================================================
+#ifndef ESC_SWEEP_ILP
+#define ESC_SWEEP_ILP 8
+#endif
+static constexpr int SWEEP_ILP = ESC_SWEEP_ILP;   // independent accesses in flight per lane (4- and 5-cycles)
+// The pair sweep runs three 512-thread CTAs per SM (40 registers a thread),
+// which leaves room for fewer accesses in flight per lane.
+#ifndef ESC_PAIR_ILP
+#define ESC_PAIR_ILP 4
+#endif
+static constexpr int PAIR_ILP = ESC_PAIR_ILP;
+static constexpr int PAIR_CTAS_PER_SM = 3;
+
+struct SweepScratch {
+  uint32_t* cnt;       // per CTA: n counters (kept zero between items)
+  int32_t* touched;    // per CTA: n entries
+  uint32_t* cnt2;      // second counter array (5-cycles)
+  int32_t* touched2;
+  unsigned* ntouched;  // per CTA: 2 counters
+  int64_t n;
+};
+
+template <bool BIG>
+__global__ void k_cycles4(DevGraph g, unsigned long long* qctr, TagScratch ts, unsigned long long* C4raw,
+                          unsigned long long* C4v, AccSet acc) {
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  TaggedCounters<BIG> w(ts);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u128 c4sum = 0;
+  while (true) {
+    int64_t it = next_item(qctr, g.n, &sh_item);
+    if (it < 0) break;
+    int64_t i = g.n - 1 - it;
+    int64_t b0 = g.R[i], e0 = g.op[i];
+    if (e0 == b0) continue;           // no lower neighbours
+    if (w.next(g.n)) __syncthreads();
+    // pass 1: wedge counts w(i, j).  C(w, 2) at j is the sum of the values the
+    // increments of j return, so each increment adds its old value to C4(j)
+    // at once and no second pass over the touched j's is needed.  The lists
+    // N(k) below i are fetched 32 per warp (lane l the l-th), SWEEP_ILP
+    // entries in flight per lane.
+    u128 mine = 0;
+    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
+      int64_t p = pbase + (int64_t)lane * nw;
+      int64_t kb_l = 0, ke_l = 0;
+      if (p < e0) {
+        kb_l = g.R[g.C[p]];
+        ke_l = g.rev[p];                        // N(k) below i ends at the slot of i
+      }
+      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
+      for (int kk = 0; kk < kmax; ++kk) {
+        int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
+        for (int64_t q = kb + lane; q < ke; q += 32 * SWEEP_ILP) {
+          int32_t jj[SWEEP_ILP];
+          uint32_t oo[SWEEP_ILP];
+#pragma unroll
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
+#pragma unroll
+          for (int u = 0; u < SWEEP_ILP; ++u) oo[u] = jj[u] >= 0 ? w.inc(jj[u]) : 0u;
+#pragma unroll
+          for (int u = 0; u < SWEEP_ILP; ++u)
+            if (oo[u]) {
+              atomicAdd(&C4v[jj[u]], (unsigned long long)oo[u]);
+              mine += oo[u];
+            }
+        }
+      }
+    }
+    u128 tot = block_sum_u128(mine, sh);        // its barriers also end pass 1
+    if (threadIdx.x == 0) {
+      if (tot) atomicAdd(&C4v[i], (unsigned long long)tot);
+      if (acc.vg) acc_add(acc_of(acc, i), ACC_C4, tot);
+      else c4sum += tot;
+    }
+    // pass 3: per-edge counts, the lists fetched as in pass 1
+    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
+      int64_t p_l = pbase + (int64_t)lane * nw;
+      int64_t kb_l = 0, ke_l = 0;
+      int32_t k_l = 0;
+      if (p_l < e0) {
+        k_l = g.C[p_l];
+        kb_l = g.R[k_l];
+        ke_l = g.rev[p_l];
+      }
+      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
+      for (int kk = 0; kk < kmax; ++kk) {
+        int64_t kb = __shfl_sync(0xffffffffu, kb_l, kk), ke = __shfl_sync(0xffffffffu, ke_l, kk);
+        unsigned long long sk = 0;
+        for (int64_t q = kb + lane; q < ke; q += 32 * SWEEP_ILP) {
+          int32_t jj[SWEEP_ILP];
+#pragma unroll
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ke ? g.C[q + 32 * u] : -1;
+#pragma unroll
+          for (int u = 0; u < SWEEP_ILP; ++u) {
+            if (jj[u] < 0) continue;
+            unsigned long long c = w.get(jj[u]) - 1;
+            if (c) { atomicAdd(&C4raw[q + 32 * u], c); sk += c; }
+          }
+        }
+        sk = warp_sum_u64(sk);
+        int32_t k = __shfl_sync(0xffffffffu, k_l, kk);
+        if (lane == 0 && sk) {
+          atomicAdd(&C4raw[pbase + (int64_t)kk * nw], sk);
+          atomicAdd(&C4v[k], sk);
+        }
+      }
+    }
+    __syncthreads();                            // the next item's counts must not meet these reads
+  }
+  if (threadIdx.x == 0 && !acc.vg) acc_add(acc.base, ACC_C4, c4sum);
+}
+
+// Per-edge common-neighbour lists (built by the triangle-list pass).
+struct TriLists {
+  const int64_t* off;    // per slot: start of the edge's id list (both slots of an edge share it)
+  const int32_t* U;      // sorted common-neighbour ids
+  const int64_t* offp;   // per slot: start of the slot's position list
+  const int32_t* P;      // per slot (u -> v): positions in row u of the common neighbours, ascending
+};
+
+// ============================================================================
+// Thm 11/12: N13 = sum_{j<i} C(W(i,j), 3) and
+// N17 = sum_{j<i} (W(i,j) - 2) cc(i,j), cc = edges inside N(i) cap N(j).
+// W(i,.) from every wedge i - c - j (c in N(i), j in N(c), j < i); C(W,3) is
+// accumulated on the fly as the sum of C(old, 2) over the increments.  The cc
+// term is gathered per diamond: for each triangle {i, x, y} (x < y, y reached
+// through the position list of (x, i), so its slot in row x is direct) and each
+// j in N(x) cap N(y) below i, add W(i,j) - 2 (Thm 12's enumeration through the
+// per-edge triangle lists).
+// ============================================================================
 
 
 template <bool BIG>
@@ -1813,15 +1810,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
 
   // sweep scratch: one set per concurrent sweep (4-cycles; pairs and the
   // tagged 5-cycle counters are sized below, once the largest degree is known)
-  DevBuf b_cntA, b_tlA, b_cntB, b_cntC, b_cntD, b_tlD, b_ntA, b_ntC;
+  DevBuf b_cntA, b_cntB, b_cntC, b_cntD, b_tlD, b_ntC;
   size_t sw = sizeof(uint32_t) * (size_t)n * grid_sweep + 16;
-  ESC_TRY(b_cntA.alloc(sw)); ESC_TRY(b_tlA.alloc(sw));
   ESC_TRY(b_cntD.alloc(sw)); ESC_TRY(b_tlD.alloc(sw));
-  ESC_TRY(b_ntA.alloc(sizeof(unsigned) * 2 * grid_sweep));
   ESC_TRY(b_ntC.alloc(sizeof(unsigned) * 2 * grid_sweep));
-  cudaMemsetAsync(b_cntA.p, 0, sw, s);
   cudaMemsetAsync(b_cntD.p, 0, sw, s);
-  SweepScratch ssA{b_cntA.as<uint32_t>(), b_tlA.as<int32_t>(), nullptr, nullptr, b_ntA.as<unsigned>(), n};
 
   // common-neighbour list offsets and sizes
   DevBuf b_off, b_offp, b_U, b_P, b_gh;
@@ -1843,7 +1836,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
   int64_t maxdeg = n > 0 ? hR[n] - hR[n - 1] : 0;   // the highest rank has the largest degree
-  // pair and 5-cycle sweeps: tagged counters, 32-bit words below the first
+  // 4-cycle, pair and 5-cycle sweeps: tagged counters, 32-bit words below the first
   // rank of degree >= 2^16, 64-bit words from there on
   int64_t jbig = n;
   {
@@ -1858,13 +1851,17 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   size_t sw64 = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_sweep + 16;
   size_t sw32p = sizeof(uint32_t) * (size_t)jbig * grid_pairs + 16;
   size_t sw64p = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_pairs + 16;
-  DevBuf b_bigB, b_bigC;
+  DevBuf b_bigA, b_bigB, b_bigC;
+  ESC_TRY(b_cntA.alloc(sw32)); ESC_TRY(b_bigA.alloc(sw64));
   ESC_TRY(b_cntB.alloc(sw32p)); ESC_TRY(b_bigB.alloc(sw64p));
   ESC_TRY(b_cntC.alloc(sw32)); ESC_TRY(b_bigC.alloc(sw64));
+  cudaMemsetAsync(b_cntA.p, 0, sw32, s);
   cudaMemsetAsync(b_cntB.p, 0, sw32p, s);
   cudaMemsetAsync(b_cntC.p, 0, sw32, s);
+  cudaMemsetAsync(b_bigA.p, 0, sw64, s);
   cudaMemsetAsync(b_bigB.p, 0, sw64p, s);
   cudaMemsetAsync(b_bigC.p, 0, sw64, s);
+  TagScratch tsA{b_cntA.as<uint32_t>(), b_bigA.as<unsigned long long>(), jbig, n};
   TagScratch tsB{b_cntB.as<uint32_t>(), b_bigB.as<unsigned long long>(), jbig, n};
   TagScratch tsC{b_cntC.as<uint32_t>(), b_bigC.as<unsigned long long>(), jbig, n};
   SweepScratch ssC{nullptr, nullptr, b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(), b_ntC.as<unsigned>(), n};
@@ -1970,7 +1967,10 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // 4-cycles (Thm 5)
   mark(3, 0, s2);
   if (n > 0) {
-    (k_cycles4<<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, ssA, C4e, C4v, accs), note_launch());
+    if (jbig < n)
+      (k_cycles4<true><<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, tsA, C4e, C4v, accs), note_launch());
+    else
+      (k_cycles4<false><<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, tsA, C4e, C4v, accs), note_launch());
     (k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s2>>>(g, C4e), note_launch());
   }
   mark(3, 1, s2);

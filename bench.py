@@ -146,11 +146,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def source_digest() -> str:
-    h = hashlib.sha256()
+def source_digest(kernel: str = "k_pairs") -> str:
+    """Digest of what decides a kernel's DRAM traffic: its function text, the
+    counter struct it uses and every line naming its constants or launch
+    configuration in census.cu.  Host-side edits elsewhere leave it unchanged;
+    any edit of the kernel changes it (and a failed extraction hashes the whole
+    file, which only makes a stored figure look stale)."""
     path = os.path.join(ROOT, "paper_1610_09411_gb300", "csrc", "census.cu")
-    with open(path, "rb") as f:
-        h.update(f.read())
+    with open(path) as f:
+        src = f.read()
+    h = hashlib.sha256()
+    sig = src.find(f" {kernel}(")
+    start = src.rfind("template", 0, sig) if sig >= 0 else -1
+    end = src.find("\n}\n", sig) if sig >= 0 else -1
+    st = src.find("struct TaggedCounters {")
+    st_end = src.find("\n};\n", st) if st >= 0 else -1
+    if min(sig, start, end, st, st_end) < 0:
+        h.update(src.encode())
+        return h.hexdigest()[:16]
+    h.update(src[start:end].encode())
+    h.update(src[st:st_end].encode())
+    for line in src.splitlines():
+        if any(k in line for k in ("PAIR_ILP", "PAIR_CTAS_PER_SM", "grid_pairs", "pthreads", f"{kernel}<")):
+            h.update(line.encode())
     return h.hexdigest()[:16]
 
 
@@ -162,7 +180,7 @@ def stored_traffic(kernel: str, workload: str):
         with open(path) as f:
             t = json.load(f)
         rec = t.get(f"{kernel}:{workload}")
-        if rec and rec.get("source_sha") == source_digest():
+        if rec and rec.get("source_sha") == source_digest(kernel.split(" ")[0]):
             return rec["dram_bytes_per_launch"]
     except Exception:
         pass

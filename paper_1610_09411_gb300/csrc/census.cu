@@ -1469,16 +1469,6 @@ __global__ void k_clique_dims(DevGraph g, unsigned long long* out) {
   atomicMax(&out[1], md);
 }
 
-size_t census_scratch_bytes(int64_t n, int64_t nnz, int sms, int cta_per_sm) {
-  (void)sms; (void)cta_per_sm;
-  return 0;   // scratch is allocated inside run_census (sizes depend on the graph)
-}
-
-static cudaError_t check_status(unsigned* d_status, cudaStream_t s, unsigned* h) {
-  cudaError_t e = cudaMemcpyAsync(h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e;
-}
 
 // ---------------------------------------------------------------- buffers
 // Device buffers of one census.  Repeated censuses would otherwise pay dozens
@@ -1644,9 +1634,9 @@ static cudaError_t allow_max_smem(const void* k, int optin) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
-cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, void* /*scratch*/,
-                       size_t /*scratch_bytes*/, const CensusConfig& cfg, unsigned long long* d_out,
-                       unsigned* d_status, PerElement* pe_out, Oriented* or_out, cudaStream_t s) {
+cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, const CensusConfig& cfg,
+                       unsigned long long* d_out, unsigned* d_status, PerElement* pe_out, Oriented* or_out,
+                       cudaStream_t s) {
   CacheScope cache_scope(s);                    // destroyed last: the buffers below return after the stream drains
   const int sms = cfg.sms > 0 ? cfg.sms : 1;
   int smem_optin = 0;

@@ -183,11 +183,6 @@ int device_sms(int dev) {
   return sms > 0 ? sms : 1;
 }
 
-__global__ void k_rebase_rows(const int64_t* rp, int64_t n, int64_t base, int64_t* out) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) out[i] = rp[i] - base;
-}
-
 // batch: local ids of graph k's rows become union ids (add the graph's first
 // vertex); an id outside its own graph is flagged and left in range
 __global__ void k_globalize(const int64_t* voff, int num_graphs, const int64_t* rp, int64_t rows, int32_t* col,
@@ -260,7 +255,7 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   cfg.serial_phases = g->serial > 0 || (g->serial < 0 && nnz >= ((int64_t)1 << 24));
   cfg.phase_events = nev ? evs : nullptr;
   cfg.num_phase_events = nev;
-  e = esc::run_census(d_rp, d_col, n, nnz, nullptr, 0, cfg, d_out, d_status, keep ? pe : nullptr,
+  e = esc::run_census(d_rp, d_col, n, nnz, cfg, d_out, d_status, keep ? pe : nullptr,
                       keep ? ori : nullptr, s);
   escape_status st = from_cuda(e);
   unsigned hstat = 0;
@@ -501,7 +496,7 @@ escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offset
     cfg.cta_per_sm = 2;
     cfg.d_vtx_offsets = d_voff;
     cfg.num_graphs = num_graphs;
-    e = esc::run_census(d_rp, d_col, rows, nnz, nullptr, 0, cfg, d_out, d_status, nullptr, nullptr, s);
+    e = esc::run_census(d_rp, d_col, rows, nnz, cfg, d_out, d_status, nullptr, nullptr, s);
     st = from_cuda(e);
     unsigned h = 0;
     if (st == ESCAPE_OK) {

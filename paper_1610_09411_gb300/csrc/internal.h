@@ -71,7 +71,8 @@ struct CensusTimings {
 // Runs the whole census (orientation through conversion) for one graph held in
 // device memory (original ids), writing 2 x 49 u128 counts (induced 4+11+34,
 // then non-induced) to `d_out` (device) and, when `pe` is non-null, keeping the
-// per-element arrays.  `scratch` is sized by census_scratch_bytes().
+// per-element arrays.  Work space comes from the library's device-buffer
+// cache (allocated inside, sized from the graph).
 struct CensusConfig {
   int sms = 0;                    // SM count of the device
   int cta_per_sm = 2;             // persistent CTAs per SM for the sweep kernels
@@ -86,10 +87,9 @@ struct CensusConfig {
   int num_graphs = 1;
 };
 
-size_t census_scratch_bytes(int64_t n, int64_t nnz, int sms, int cta_per_sm);
-cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, void* scratch,
-                       size_t scratch_bytes, const CensusConfig& cfg, unsigned long long* d_out, unsigned* d_status,
-                       PerElement* pe_out, Oriented* or_out, cudaStream_t s);
+cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, const CensusConfig& cfg,
+                       unsigned long long* d_out, unsigned* d_status, PerElement* pe_out, Oriented* or_out,
+                       cudaStream_t s);
 
 // Conversion tables (App. B), built on the host by this library's own
 // embedding count over the pattern catalogue.

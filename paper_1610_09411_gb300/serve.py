@@ -29,12 +29,16 @@ def footprint_bytes(n: int, m: int, sms: int = 152, cta_per_sm: int = 2) -> int:
     """Conservative device bytes for the census of one graph (n vertices, m
     edges): the CSR and its renamed copy, per-edge arrays and common-neighbour
     lists (bounded by the edge count times a triangle factor), and the sweep
-    scratch that grows with n.  Used for admission only."""
+    scratch that grows with n: per persistent CTA, 4 B per vertex for each of
+    the tagged 4-cycle, pair and 5-cycle counters (the pair sweep runs three
+    CTAs per SM), 8 B for the 5-cycle P2 counters and their list, and 8 B for
+    the wheel counters of large centres (their degree is at most n).  Used for
+    admission only."""
     nnz = 2 * m
     per_edge = nnz * (4 + 4 + 8 + 8 + 8 + 8 + 8 + 8)      # col x2, rev, T, K4, C4, offsets x2
     lists = nnz * 4 * 12                                    # id and position lists (triangle factor)
     per_vertex = n * 8 * 12
-    sweep = 4 * n * 4 * sms * cta_per_sm                    # four dense counter / touched arrays
+    sweep = n * sms * ((4 + 4 + 8) * cta_per_sm + 4 * 3 + 8 * 2)
     return int(per_edge + lists + per_vertex + sweep + (64 << 20))
 
 

@@ -46,6 +46,11 @@ typedef struct {
   escape_u128 n3[4], n4[11], n5[34];   /* non-induced counts (Sec. 3.1)             */
 } escape_census;
 
+typedef struct {                       /* the 3- and 4-vertex part of escape_census */
+  escape_u128 c3[4], c4[11];
+  escape_u128 n3[4], n4[11];
+} escape_census34;
+
 typedef enum {
   ESCAPE_OK = 0,
   ESCAPE_EINVAL = 1,     /* invalid argument or malformed graph                     */
@@ -95,6 +100,19 @@ escape_status escape_graph_info(const escape_graph* g, int64_t* n, int64_t* m);
  * Graphs with n < 5, no edges, or no triangles are valid.
  */
 escape_status escape_census5(escape_graph* g, escape_census* out, void* stream);
+
+/*
+ * escape_census4 -- the 3- and 4-vertex census alone (Thm 1; the paper's
+ * section on counting 4-vertex patterns): the same counts as the c3, c4, n3,
+ * n4 fields of escape_census5, computed from the degree sums, triangles,
+ * 4-cycles and 4-cliques only, without the common-neighbour lists, pair,
+ * wheel and 5-cycle sweeps that the 5-vertex counts need.
+ *   out      host memory; written only on success.
+ * Options, per-element arrays (escape_per_element: T, C4 and K4 are all
+ * computed here), phase times and errors as for escape_census5; the skipped
+ * phases report 0 ms.
+ */
+escape_status escape_census4(escape_graph* g, escape_census34* out, void* stream);
 
 /*
  * escape_census5_batch -- census of many small graphs given as one block

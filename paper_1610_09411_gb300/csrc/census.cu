@@ -295,7 +295,7 @@ struct CliqueScratch {
 
 // B rows are symmetric (row a = every neighbour of v_a inside N+(x)).
 __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int b, const uint64_t* Da,
-                                            const uint64_t* Db, int DW, unsigned long long& alpha_out,
+                                            const uint64_t* Db, int DW, bool with_k5, unsigned long long& alpha_out,
                                             unsigned long long& beta_out, unsigned long long& k5_out) {
   const uint64_t* ra = B + (int64_t)a * W;
   const uint64_t* rb = B + (int64_t)b * W;
@@ -303,7 +303,7 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int
   for (int w = 0; w < W; ++w) alpha += __popcll(ra[w] & rb[w]);
   // 5-cliques with lowest vertex x and next two v_a < v_b: every c in the
   // common neighbourhood above b, then every l adjacent to a, b, c above c
-  int w0 = (b + 1) >> 6;
+  int w0 = with_k5 ? (b + 1) >> 6 : W;
   for (int w = w0; w < W; ++w) {
     uint64_t cm = ra[w] & rb[w];
     if (w == w0) cm &= ~0ull << ((b + 1) & 63);
@@ -330,7 +330,7 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int
 // B (d x W u64), K4 accumulators (d u64), T of x's out-edges (d u32).
 __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
                                const uint32_t* T, unsigned long long* K4e, AccSet acc, CliqueScratch cs,
-                               int hash_cap, int dmax, unsigned* status) {
+                               int hash_cap, int dmax, unsigned* status, bool with_k5) {
   extern __shared__ uint64_t smem64[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
@@ -404,7 +404,7 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
         if (b < 0) continue;
         unsigned long long alpha, beta, k5;
         clique_edge(B, W, a, b, use_beta ? D + (int64_t)a * DW : nullptr, use_beta ? D + (int64_t)b * DW : nullptr,
-                    DW, alpha, beta, k5);
+                    DW, with_k5, alpha, beta, k5);
         unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
         unsigned long long tab = T[q], txa = Tx[a], txb = Tx[b];
         la.v[0] += alpha;                                         // 3 x K4
@@ -441,7 +441,7 @@ static constexpr int CLQ_ILP = 4;
 
 __global__ void __launch_bounds__(CLQ_WARPS * 32, 4) k_clique_warp(DevGraph g, const int32_t* items, int64_t nitems,
                                                                 unsigned long long* qctr, const uint32_t* T,
-                                                                unsigned long long* K4e, AccSet acc) {
+                                                                unsigned long long* K4e, AccSet acc, bool with_k5) {
   __shared__ u128 sh[32];
   __shared__ int32_t sL[CLQ_WARPS][32];
   __shared__ uint32_t sT[CLQ_WARPS][32];
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(CLQ_WARPS * 32, 4) k_clique_warp(DevGraph g, c
         for (int t = 0; t < DW; ++t) beta += (unsigned long long)__popcll(sD[wl][lane][t] & sD[wl][b][t]);
         // 5-cliques at the three lowest vertices x, v_a, v_b: every c in the
         // common neighbourhood above b, then every l adjacent to a, b, c above c
-        unsigned long long cm2 = cm & (~0ull << (b + 1));
+        unsigned long long cm2 = with_k5 ? cm & (~0ull << (b + 1)) : 0ull;
         while (cm2) {
           int c = __ffsll((long long)cm2) - 1;
           cm2 &= cm2 - 1;
@@ -1800,8 +1800,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
 
   // sweep scratch: one set per concurrent sweep (4-cycles; pairs and the
   // tagged 5-cycle counters are sized below, once the largest degree is known)
+  // With four_only, only the 4-cycle sweep runs; the lists, pairs, wheels and
+  // 5-cycles (and their work space) are skipped.
+  const bool five = !cfg.four_only;
   DevBuf b_cntA, b_cntB, b_cntC, b_cntD, b_tlD, b_ntC;
-  size_t sw = sizeof(uint32_t) * (size_t)n * grid_sweep + 16;
+  size_t sw = five ? sizeof(uint32_t) * (size_t)n * grid_sweep + 16 : 16;
   ESC_TRY(b_cntD.alloc(sw)); ESC_TRY(b_tlD.alloc(sw));
   ESC_TRY(b_ntC.alloc(sizeof(unsigned) * 2 * grid_sweep));
   cudaMemsetAsync(b_cntD.p, 0, sw, s);
@@ -1812,17 +1815,19 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(b_offp.alloc(sizeof(int64_t) * (nnz + 2)));
   int64_t* off = b_off.as<int64_t>();
   int64_t* offp = b_offp.as<int64_t>();
-  if (n > 0) (k_canon_counts<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, off), note_launch());
-  ESC_TRY(exclusive_scan_i64(off, off, nnz, true, arena, s));
-  if (n > 0) (k_all_counts<<<grid_for(nnz, TPB, sms), TPB, 0, s>>>(T, nnz, offp), note_launch());
-  ESC_TRY(exclusive_scan_i64(offp, offp, nnz, true, arena, s));
   int64_t ulen = 0, plen = 0;
+  if (five) {
+    if (n > 0) (k_canon_counts<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, off), note_launch());
+    ESC_TRY(exclusive_scan_i64(off, off, nnz, true, arena, s));
+    if (n > 0) (k_all_counts<<<grid_for(nnz, TPB, sms), TPB, 0, s>>>(T, nnz, offp), note_launch());
+    ESC_TRY(exclusive_scan_i64(offp, offp, nnz, true, arena, s));
+    cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&plen, offp + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  }
   std::vector<int64_t> hR(n + 1, 0);
-  cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&plen, offp + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (n > 0) cudaMemcpyAsync(hR.data(), o.R, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
-  if (n > 0) (k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off), note_launch());
+  if (five && n > 0) (k_share_offsets<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, off), note_launch());
   ESC_TRY(b_U.alloc(sizeof(int32_t) * (ulen + 1)));
   ESC_TRY(b_P.alloc(sizeof(int32_t) * (plen + 1)));
   int64_t maxdeg = n > 0 ? hR[n] - hR[n - 1] : 0;   // the highest rank has the largest degree
@@ -1839,18 +1844,19 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   const int grid_pairs = sms * (cfg.cta_per_sm == 2 ? PAIR_CTAS_PER_SM : std::max(1, cfg.cta_per_sm));
   size_t sw32 = sizeof(uint32_t) * (size_t)jbig * grid_sweep + 16;
   size_t sw64 = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_sweep + 16;
-  size_t sw32p = sizeof(uint32_t) * (size_t)jbig * grid_pairs + 16;
-  size_t sw64p = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_pairs + 16;
+  size_t sw32p = five ? sizeof(uint32_t) * (size_t)jbig * grid_pairs + 16 : 16;
+  size_t sw64p = five ? sizeof(unsigned long long) * (size_t)(n - jbig) * grid_pairs + 16 : 16;
+  size_t sw32c = five ? sw32 : 16, sw64c = five ? sw64 : 16;
   DevBuf b_bigA, b_bigB, b_bigC;
   ESC_TRY(b_cntA.alloc(sw32)); ESC_TRY(b_bigA.alloc(sw64));
   ESC_TRY(b_cntB.alloc(sw32p)); ESC_TRY(b_bigB.alloc(sw64p));
-  ESC_TRY(b_cntC.alloc(sw32)); ESC_TRY(b_bigC.alloc(sw64));
+  ESC_TRY(b_cntC.alloc(sw32c)); ESC_TRY(b_bigC.alloc(sw64c));
   cudaMemsetAsync(b_cntA.p, 0, sw32, s);
   cudaMemsetAsync(b_cntB.p, 0, sw32p, s);
-  cudaMemsetAsync(b_cntC.p, 0, sw32, s);
+  cudaMemsetAsync(b_cntC.p, 0, sw32c, s);
   cudaMemsetAsync(b_bigA.p, 0, sw64, s);
   cudaMemsetAsync(b_bigB.p, 0, sw64p, s);
-  cudaMemsetAsync(b_bigC.p, 0, sw64, s);
+  cudaMemsetAsync(b_bigC.p, 0, sw64c, s);
   TagScratch tsA{b_cntA.as<uint32_t>(), b_bigA.as<unsigned long long>(), jbig, n};
   TagScratch tsB{b_cntB.as<uint32_t>(), b_bigB.as<unsigned long long>(), jbig, n};
   TagScratch tsC{b_cntC.as<uint32_t>(), b_bigC.as<unsigned long long>(), jbig, n};
@@ -1858,7 +1864,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   const int hcap_l = 8192;
   int64_t ghash_cap = pow2_at_least((int)std::max<int64_t>(2 * maxdeg, 2));
   if (2 * maxdeg <= hcap_l) ghash_cap = 2;
-  ESC_TRY(b_gh.alloc(sizeof(int32_t) * 2 * (size_t)ghash_cap * grid_sweep + 16));
+  ESC_TRY(b_gh.alloc(five ? sizeof(int32_t) * 2 * (size_t)ghash_cap * grid_sweep + 16 : 16));
   size_t smem_l = sizeof(int32_t) * 2 * (size_t)hcap_l;
   ESC_TRY(allow_max_smem((const void*)k_tri_lists, smem_optin));
   TriLists tl3{off, b_U.as<int32_t>(), offp, b_P.as<int32_t>()};
@@ -1878,7 +1884,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   int64_t gstride = maxdeg > smem_cap ? maxdeg : 1;
   size_t smem_w = sizeof(uint32_t) * (size_t)std::max(smem_cap, 1);
   std::vector<int64_t> item_off(n - c0 + 1, 0);
-  if (c0 < n) {
+  if (five && c0 < n) {
     for (int64_t c = c0; c < n; ++c)
       item_off[c - c0 + 1] = item_off[c - c0] + (hR[c + 1] - hR[c] + WHEEL_CHUNK - 1) / WHEEL_CHUNK;
     nitems_w = item_off[n - c0];
@@ -1889,7 +1895,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     ESC_TRY(allow_max_smem((const void*)k_wheels_cta, smem_optin));
   }
   DevBuf b_wo;                                 // warp wheel items: offsets over centres c0-1 .. 0
-  if (c0 > 0) {
+  if (five && c0 > 0) {
     ESC_TRY(b_wo.alloc(sizeof(int64_t) * (size_t)(c0 + 1)));
     (k_wheel_warp_counts<<<grid_for(c0, TPB, sms), TPB, 0, s>>>(g, c0, b_wo.as<int64_t>()), note_launch());
     ESC_TRY(exclusive_scan_i64(b_wo.as<int64_t>(), b_wo.as<int64_t>(), c0, true, arena, s));
@@ -1900,7 +1906,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   //   s3 (most urgent): wheels      s : pairs
   //   s1, s2, s4 (least urgent): cliques, 4-cycles, 5-cycles; s joins all.
   mark(4, 0, s);
-  if (n > 0)
+  if (five && n > 0)
     (k_tri_lists<<<grid_sweep, 512, smem_l, s>>>(g, ctr + 3, off, offp, T, b_U.as<int32_t>(), b_P.as<int32_t>(),
                                                  b_gh.as<int32_t>(), ghash_cap, hcap_l, d_status), note_launch());
   mark(4, 1, s);
@@ -1915,10 +1921,10 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
 
   // wheels (Thm 11): the longest phase, started first
   mark(6, 0, s3);
-  if (c0 < n)
+  if (five && c0 < n)
     (k_wheels_cta<<<2 * sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
                                             b_gs.as<unsigned long long>(), gstride, smem_cap, accs), note_launch());
-  if (c0 > 0) {
+  if (five && c0 > 0) {
     int per_sm = 1;
     ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wheels_warp, 256, 0));
     (k_wheels_warp<<<(unsigned)std::max(1, per_sm) * sms, 256, 0, s3>>>(g, c0, b_wo.as<int64_t>(), ctr + 7, tl3, T,
@@ -1927,7 +1933,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(6, 1, s3);
   // pairs (Thms 11, 12); 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
   mark(5, 0, s);
-  if (n > 0) {
+  if (five && n > 0) {
     // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can);
     // whole warps only: the kernel's reductions shuffle across full warps
     int pthreads = cfg.cta_per_sm == 2 ? 512 : std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
@@ -1941,13 +1947,13 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(2, 0, s1);
   if (nitems_b > 0)
     (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), clq_threads, smem_b, s1>>>(
-        g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, dmax, d_status), note_launch());
+        g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, dmax, d_status, five), note_launch());
   if (nwsmall > 0) {
     int per_sm = 1;
     ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_warp, CLQ_WARPS * 32, 0));
     unsigned grid_w = (unsigned)std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, (nwsmall + CLQ_WARPS - 1) / CLQ_WARPS);
-    (k_clique_warp<<<grid_w, CLQ_WARPS * 32, 0, s1>>>(g, b_wsmall.as<int32_t>(), nwsmall, ctr + 8, T, K4e, accs),
-     note_launch());
+    (k_clique_warp<<<grid_w, CLQ_WARPS * 32, 0, s1>>>(g, b_wsmall.as<int32_t>(), nwsmall, ctr + 8, T, K4e, accs,
+                                                      five), note_launch());
   }
   if (n > 0) {
     (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e), note_launch());
@@ -1966,7 +1972,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(3, 1, s2);
   // 5-cycles (Thm 13)
   mark(7, 0, s4);
-  if (n > 0) {
+  if (five && n > 0) {
     if (jbig < n)
       (k_cycles5<true><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs), note_launch());
     else

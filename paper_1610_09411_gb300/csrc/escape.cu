@@ -236,7 +236,7 @@ __global__ void k_map_vertices(int64_t n, const int32_t* rank, const unsigned lo
 
 escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_col, int64_t n, int64_t nnz,
                          escape_census* out, cudaStream_t s, bool keep, esc::PerElement* pe, esc::Oriented* ori,
-                         float* phase_ms, int* nphase) {
+                         float* phase_ms, int* nphase, bool four_only = false) {
   unsigned long long* d_out = nullptr;
   unsigned* d_status = nullptr;
   cudaError_t e = cudaMalloc(&d_out, sizeof(escape_census));
@@ -255,6 +255,7 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   cfg.serial_phases = g->serial > 0 || (g->serial < 0 && nnz >= ((int64_t)1 << 24));
   cfg.phase_events = nev ? evs : nullptr;
   cfg.num_phase_events = nev;
+  cfg.four_only = four_only;
   e = esc::run_census(d_rp, d_col, n, nnz, cfg, d_out, d_status, keep ? pe : nullptr,
                       keep ? ori : nullptr, s);
   escape_status st = from_cuda(e);
@@ -403,6 +404,24 @@ escape_status escape_census5(escape_graph* g, escape_census* out, void* stream) 
   escape_status st = census_one(g, g->d_rp, g->d_col, g->n, g->nnz, out, s, g->keep_pe != 0, &g->pe, &g->ori,
                                 g->phase_ms, &g->num_phases);
   g->launches = esc::launches_so_far() - l0;
+  if (st == ESCAPE_OK && g->keep_pe) g->has_pe = true;
+  else free_pe(g);
+  return st;
+}
+
+escape_status escape_census4(escape_graph* g, escape_census34* out, void* stream) {
+  if (!g || !out) return ESCAPE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  free_pe(g);
+  long long l0 = esc::launches_so_far();
+  escape_census full;
+  escape_status st = census_one(g, g->d_rp, g->d_col, g->n, g->nnz, &full, s, g->keep_pe != 0, &g->pe, &g->ori,
+                                g->phase_ms, &g->num_phases, true);
+  g->launches = esc::launches_so_far() - l0;
+  if (st == ESCAPE_OK) {
+    for (int i = 0; i < 4; ++i) { out->c3[i] = full.c3[i]; out->n3[i] = full.n3[i]; }
+    for (int i = 0; i < 11; ++i) { out->c4[i] = full.c4[i]; out->n4[i] = full.n4[i]; }
+  }
   if (st == ESCAPE_OK && g->keep_pe) g->has_pe = true;
   else free_pe(g);
   return st;

@@ -78,6 +78,7 @@ struct CensusConfig {
   int cta_per_sm = 2;             // persistent CTAs per SM for the sweep kernels
   bool keep_per_element = false;
   bool serial_phases = false;     // run every phase on the caller's stream, one after another
+  bool four_only = false;         // 3- and 4-vertex counts only: skip the lists, pairs, wheels and 5-cycles
   cudaEvent_t* phase_events = nullptr;   // optional: records an event after each phase
   int num_phase_events = 0;
   // batch: the graph is the block-diagonal union of num_graphs graphs whose

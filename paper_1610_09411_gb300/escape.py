@@ -46,6 +46,15 @@ class Census(ctypes.Structure):
         return {k: ints(getattr(self, k)) for k in ("c3", "c4", "c5", "n3", "n4", "n5")}
 
 
+class Census4(ctypes.Structure):
+    _fields_ = [("c3", U128 * 4), ("c4", U128 * 11), ("n3", U128 * 4), ("n4", U128 * 11)]
+
+    def to_dict(self) -> dict:
+        def ints(arr):
+            return [int(x.lo) | (int(x.hi) << 64) for x in arr]
+        return {k: ints(getattr(self, k)) for k in ("c3", "c4", "n3", "n4")}
+
+
 def _load():
     lib_path = _build.LIB
     if not os.path.exists(lib_path):
@@ -56,6 +65,8 @@ def _load():
     lib.escape_load_csr.argtypes = [i64, i64, P, P, u32, P, ctypes.POINTER(P)]
     lib.escape_graph_info.restype = c_int
     lib.escape_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.escape_census4.restype = c_int
+    lib.escape_census4.argtypes = [P, ctypes.POINTER(Census4), P]
     lib.escape_census5.restype = c_int
     lib.escape_census5.argtypes = [P, ctypes.POINTER(Census), P]
     lib.escape_census5_batch.restype = c_int
@@ -149,6 +160,13 @@ def escape_set_options(h, keep_per_element: bool = False, cta_per_sm: int = 0, s
     """serial_phases: True / False, or None for the size-based default."""
     sp = -1 if serial_phases is None else int(bool(serial_phases))
     _check(LIB.escape_set_options(h, int(bool(keep_per_element)), int(cta_per_sm), sp), "escape_set_options")
+
+
+def escape_census4(h, stream=None) -> dict:
+    """The 3- and 4-vertex census alone (keys c3, c4, n3, n4)."""
+    out = Census4()
+    _check(LIB.escape_census4(h, ctypes.byref(out), _stream(stream)), "escape_census4")
+    return out.to_dict()
 
 
 def escape_census5(h, stream=None) -> dict:

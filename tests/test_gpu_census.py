@@ -127,6 +127,34 @@ def test_two_hubs_wide_counts():
     assert_same_census(got, want)
 
 
+@pytest.mark.parametrize("make", [lambda: gg.config_er500(1), lambda: gg.complete(40),
+                                  lambda: gg.chung_lu(20000, 2.1, 10, 2000, 4), lambda: gg.barabasi_albert(3000, 5, 2),
+                                  lambda: gg.disjoint_union([gg.star(3000), gg.complete(70), gg.empty(4)]),
+                                  lambda: gg.empty(3)],
+                         ids=["er500", "K40", "cl20000", "ba3000", "star_union", "empty3"])
+def test_census4_alone(make):
+    """escape_census4 (the 3- and 4-vertex census without the 5-vertex
+    sweeps) gives the oracle's counts, the same as the 3- and 4-vertex part of
+    escape_census5, and the same per-element arrays."""
+    from paper_1610_09411_gb300 import escape as esc
+    g = make()
+    h = esc.escape_load_csr(g.n, g.row_ptr, g.col)
+    try:
+        esc.escape_set_options(h, True)
+        r4 = esc.escape_census4(h)
+        pe4 = esc.escape_per_element(h) if g.m > 0 else None
+        r5 = esc.escape_census5(h)
+        pe5 = esc.escape_per_element(h) if g.m > 0 else None
+    finally:
+        esc.escape_free(h)
+    keys = ("c3", "c4", "n3", "n4")
+    assert_same_census(r4, r5, keys)
+    assert_same_census(r4, oracle.census(g), keys)
+    if pe4 is not None:
+        for k in pe4:
+            assert np.array_equal(pe4[k], pe5[k]), k
+
+
 def test_censuses_on_concurrent_host_threads():
     """Censuses issued at the same time from several host threads, each on its
     own stream, over graphs whose kernels need different shared-memory sizes

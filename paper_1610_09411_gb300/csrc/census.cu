@@ -8,8 +8,8 @@
 //   Thm 4, 8, 9 degree/edge closed forms ...... k_vertex_basic, k_edge_sums
 //   Thm 7 triangles T(e), t(i) ................ k_tri_small / k_tri_large (pass A)
 //   Thm 6/7 4-cliques K4(e), K4(t); Thm 10 N10,
-//     N16, N20; Thm 14 5-cliques; Thm 13's
-//     directed tailed triangles ................ k_clique_large (pass B)
+//     N16, N20; Thm 14 5-cliques ............... k_clique_warp / k_clique_large (pass B)
+//   Thm 13's directed tailed triangles ......... k_tri_small / k_tri_large (pass A)
 //   Thm 5 4-cycles C4(e), C4(i) ................ k_cycles4
 //   Thm 12 common-neighbour lists of edges ..... k_tri_lists
 //   Thm 11/12 N13, N17 (pairs and diamonds) .... k_pairs

@@ -235,16 +235,18 @@ def escape_free(h):
 
 # ------------------------------------------------------------------ convenience
 
-def census(row_ptr, col, n: int | None = None, flags: int = 0, per_element: bool = False, stream=None) -> dict:
+def census(row_ptr, col, n: int | None = None, flags: int = 0, per_element: bool = False, stream=None,
+           four_only: bool = False) -> dict:
     """Load, count and free in one call.  Returns the census dict (plus
-    'per_element' when asked)."""
+    'per_element' when asked); with four_only, the 3- and 4-vertex counts
+    alone (escape_census4)."""
     if n is None:
         n = (len(row_ptr) if isinstance(row_ptr, np.ndarray) else int(row_ptr.numel())) - 1
     h = escape_load_csr(n, row_ptr, col, flags, stream)
     try:
         if per_element:
             escape_set_options(h, keep_per_element=True)
-        out = escape_census5(h, stream)
+        out = escape_census4(h, stream) if four_only else escape_census5(h, stream)
         if per_element:
             out["per_element"] = escape_per_element(h, stream)
         out["phase_ms"] = escape_last_phase_ms(h)

@@ -23,7 +23,9 @@
  *
  * Counts are exact unsigned 128-bit integers (two little-endian 64-bit words).
  *
- * Threading: a handle may be used by one thread at a time.  All calls are
+ * Threading: a handle may be used by one thread at a time; different handles
+ * may be used from different threads at the same time, each on its own stream
+ * (a serving loop with several workers does this).  All calls are
  * synchronous with respect to the host: they enqueue work on the given CUDA
  * stream (NULL = the legacy default stream) and wait for it before returning.
  * No C++ exception or exit() crosses this boundary.

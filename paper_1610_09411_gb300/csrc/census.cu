@@ -21,6 +21,15 @@
 
 #include <algorithm>
 #include <initializer_list>
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>          // header-only: no library to link
+#define ESC_HAVE_NVTX 1
+#endif
+#endif
+#ifndef ESC_HAVE_NVTX
+#define ESC_HAVE_NVTX 0
+#endif
 #include <map>
 #include <mutex>
 #include <cstdio>
@@ -1646,9 +1655,19 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   }
   // phase k is timed by events 2k (begin) and 2k+1 (end) on the stream that runs it
+  // Phase boundaries: CUDA events for the phase times, and NVTX ranges (a
+  // profiler's timeline shows each phase's launches under its name).
+  static const char* const kPhaseNames[9] = {"orient", "triangles", "cliques", "cycles4", "tri_lists",
+                                             "pairs", "wheels", "cycles5", "assemble"};
   auto mark = [&](int k, int end, cudaStream_t st) {
     int i = 2 * k + end;
     if (cfg.phase_events && i < cfg.num_phase_events) cudaEventRecord(cfg.phase_events[i], st);
+#if ESC_HAVE_NVTX
+    if (!end) nvtxRangePushA(kPhaseNames[k]);
+    else nvtxRangePop();
+#else
+    (void)kPhaseNames;
+#endif
   };
   mark(0, 0, s);
   // ---------------- orientation (Sec. 3.2)

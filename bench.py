@@ -1,14 +1,14 @@
 """Benchmark: exact 34-class 5-vertex census (plus 3-/4-vertex counts) of one
 synthetic graph per step, in edges per second.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload chung_lu|rmat22|er500]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload chung_lu|rmat22|er500|batch|serve]
   python bench.py --impl reference ...     # the CPU oracle, timed on a bounded sample
 
 One step = one escape_census5 call on a graph already resident in HBM (its
 CSR loaded once before timing): orientation, every enumeration kernel and the
 128-bit assembly.  The L2 cache is flushed (256 MB write) between steps.
 N > 1 (torchrun) runs independent replicas, one per GPU: the census of one
-graph does not shard in this build (weak scaling, value = all ranks' edges /
+graph is not sharded across GPUs (weak scaling, value = all ranks' edges /
 slowest rank's time).  One JSON line is printed by rank 0.
 """
 from __future__ import annotations

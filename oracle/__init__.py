@@ -38,8 +38,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "escape_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 NCLS = {3: 4, 4: 11, 5: 34}
 
@@ -53,38 +55,55 @@ SUM_NAMES = [
 ORACLE_ERRORS = {1: "invalid input graph", 2: "out of memory", 4: "128-bit overflow"}
 
 
-def build(force: bool = False) -> str:
-    """Compile escape_oracle.c into liboracle.so (plain gcc, portable flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile escape_oracle.c into liboracle.so (plain gcc, portable flags).
+
+    ``parallel=True`` builds liboracle_omp.so from the same source with
+    -fopenmp: the census loops over vertices run on OMP_NUM_THREADS threads
+    (the arithmetic is the same; only the order of exact additions differs).
+    The serial build is the default and the one the pins run on."""
+    lib, flags = (_LIB_OMP, ["-fopenmp"]) if parallel else (_LIB, [])
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", *flags, "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, lib)
+    return lib
 
 
-def _load():
-    global _lib
+def _load(parallel: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
-            P, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
-            lib.oracle_brute_census.restype = c_int
-            lib.oracle_brute_census.argtypes = [i64, P, P, P, P, P]
-            lib.oracle_matrix.restype = c_int
-            lib.oracle_matrix.argtypes = [c_int, P]
-            lib.oracle_classify.restype = c_int
-            lib.oracle_classify.argtypes = [c_int, c_int]
-            lib.oracle_census_sums.restype = c_int
-            lib.oracle_census_sums.argtypes = [i64, P, P, P, P, P, P, P, P, P]
-            lib.oracle_edge_elements.restype = c_int
-            lib.oracle_edge_elements.argtypes = [i64, P, P, i64, P, P, P, P, P]
-            lib.oracle_vertex_elements.restype = c_int
-            lib.oracle_vertex_elements.argtypes = [i64, P, P, i64, P, P, P]
-            lib.oracle_num_sums.restype = c_int
-            assert lib.oracle_num_sums() == len(SUM_NAMES)
+        if parallel and _lib_omp is not None:
+            return _lib_omp
+        if not parallel and _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build(parallel=parallel))
+        P, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.oracle_brute_census.restype = c_int
+        lib.oracle_brute_census.argtypes = [i64, P, P, P, P, P]
+        lib.oracle_matrix.restype = c_int
+        lib.oracle_matrix.argtypes = [c_int, P]
+        lib.oracle_classify.restype = c_int
+        lib.oracle_classify.argtypes = [c_int, c_int]
+        lib.oracle_census_sums.restype = c_int
+        lib.oracle_census_sums.argtypes = [i64, P, P, P, P, P, P, P, P, P]
+        lib.oracle_edge_elements.restype = c_int
+        lib.oracle_edge_elements.argtypes = [i64, P, P, i64, P, P, P, P, P]
+        lib.oracle_vertex_elements.restype = c_int
+        lib.oracle_vertex_elements.argtypes = [i64, P, P, i64, P, P, P]
+        lib.oracle_num_sums.restype = c_int
+        lib.oracle_num_threads.restype = c_int
+        assert lib.oracle_num_sums() == len(SUM_NAMES)
+        if parallel:
+            _lib_omp = lib
+        else:
             _lib = lib
-    return _lib
+    return lib
+
+
+def num_threads(parallel: bool = False) -> int:
+    """Threads the census of the given build runs on (1 for the serial build)."""
+    return _load(parallel).oracle_num_threads()
 
 
 def _ptr(a):
@@ -127,7 +146,7 @@ def brute_census(g) -> dict:
     return {"c3": [int(x) for x in c3], "c4": [int(x) for x in c4], "c5": [int(x) for x in c5]}
 
 
-def raw_sums(g, per_element: bool = False):
+def raw_sums(g, per_element: bool = False, parallel: bool = False):
     """The C oracle's sums (Python ints), optionally with the per-element arrays."""
     rp, col = _csr(g)
     nnz = int(rp[-1]) if g.n > 0 else 0
@@ -143,7 +162,7 @@ def raw_sums(g, per_element: bool = False):
             "K4_i": np.zeros(max(g.n, 1), dtype=np.uint64),
         }
     a = arrs or {}
-    rc = _load().oracle_census_sums(
+    rc = _load(parallel).oracle_census_sums(
         g.n, rp.ctypes.data, col.ctypes.data, sums.ctypes.data,
         _ptr(a.get("T_e")), _ptr(a.get("t_i")), _ptr(a.get("C4_e")), _ptr(a.get("C4_i")),
         _ptr(a.get("K4_e")), _ptr(a.get("K4_i")))
@@ -235,13 +254,14 @@ def induced_from_noninduced(Nd: dict) -> dict:
     return out
 
 
-def census(g, per_element: bool = False) -> dict:
+def census(g, per_element: bool = False, parallel: bool = False) -> dict:
     """Full census by the paper's method: induced (c3, c4, c5) and non-induced
-    (n3, n4, n5) counts as Python ints; optionally the per-element arrays."""
+    (n3, n4, n5) counts as Python ints; optionally the per-element arrays.
+    ``parallel=True`` runs the OpenMP build of the same source."""
     if per_element:
-        S, arrs = raw_sums(g, True)
+        S, arrs = raw_sums(g, True, parallel)
     else:
-        S, arrs = raw_sums(g, False), None
+        S, arrs = raw_sums(g, False, parallel), None
     Nd = noninduced_from_sums(S)
     out = dict(Nd)
     out.update(induced_from_noninduced(Nd))

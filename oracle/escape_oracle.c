@@ -28,6 +28,27 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the census runs on: 1 in the default (serial) build; with
+ * -fopenmp, the OpenMP thread count (OMP_NUM_THREADS). */
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+static int thread_id(void) {
+#ifdef _OPENMP
+  return omp_get_thread_num();
+#else
+  return 0;
+#endif
+}
 
 typedef unsigned __int128 u128;
 
@@ -248,9 +269,10 @@ int oracle_brute_census(int64_t n, const int64_t* rp, const int32_t* col,
 /* O2: the paper's method, written plainly.                            */
 /* ------------------------------------------------------------------ */
 static int g_ovf;
-static u128 add(u128 a, u128 b) { u128 s = a + b; if (s < a) g_ovf = 1; return s; }
+static void set_ovf(void) { __atomic_store_n(&g_ovf, 1, __ATOMIC_RELAXED); }
+static u128 add(u128 a, u128 b) { u128 s = a + b; if (s < a) set_ovf(); return s; }
 static u128 mul(u128 a, u128 b) {
-  if (a != 0 && b > ((u128)0 - 1) / a) g_ovf = 1;
+  if (a != 0 && b > ((u128)0 - 1) / a) set_ovf();
   return a * b;
 }
 static u128 ch2(uint64_t x) { return x < 2 ? 0 : (u128)x * (x - 1) / 2; }
@@ -304,17 +326,21 @@ static int64_t merge_count(const int32_t* a, int64_t na, const int32_t* b, int64
 
 static int validate(int64_t n, const int64_t* rp, const int32_t* col) {
   if (n < 0 || rp[0] != 0) return ORACLE_EINVAL;
-  for (int64_t u = 0; u < n; ++u) {
+  for (int64_t u = 0; u < n; ++u)
     if (rp[u + 1] < rp[u]) return ORACLE_EINVAL;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
+  for (int64_t u = 0; u < n; ++u)
     for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
-      if (col[p] < 0 || col[p] >= n || col[p] == u) return ORACLE_EINVAL;
-      if (p > rp[u] && col[p] <= col[p - 1]) return ORACLE_EINVAL;
+      if (col[p] < 0 || col[p] >= n || col[p] == u) bad = 1;
+      else if (p > rp[u] && col[p] <= col[p - 1]) bad = 1;
     }
-  }
+  if (bad) return ORACLE_EINVAL;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
   for (int64_t u = 0; u < n; ++u)
     for (int64_t p = rp[u]; p < rp[u + 1]; ++p)
-      if (!has_edge(rp, col, col[p], u)) return ORACLE_EINVAL;
-  return ORACLE_OK;
+      if (!has_edge(rp, col, col[p], u)) bad = 1;
+  return bad ? ORACLE_EINVAL : ORACLE_OK;
 }
 
 static void free_g(G* g) { free(g->deg); free(g->uoff); free(g->U); free(g->rev); }
@@ -328,16 +354,20 @@ static int setup(G* g, int64_t n, const int64_t* rp, const int32_t* col) {
   g->rev = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
   if (!g->deg || !g->uoff || !g->rev) return ORACLE_ENOMEM;
   for (int64_t u = 0; u < n; ++u) g->deg[u] = rp[u + 1] - rp[u];
-  /* T(e) = |N(u) cap N(v)| for every slot, then the lists themselves */
+  /* T(e) = |N(u) cap N(v)| for every slot (list offsets by a prefix sum),
+   * then the lists themselves */
   g->uoff[0] = 0;
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t u = 0; u < n; ++u)
     for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
       int64_t v = col[p];
-      g->uoff[p + 1] = g->uoff[p] + merge_count(col + rp[u], g->deg[u], col + rp[v], g->deg[v]);
+      g->uoff[p + 1] = merge_count(col + rp[u], g->deg[u], col + rp[v], g->deg[v]);
       g->rev[p] = slot_of(g, v, u);
     }
+  for (int64_t p = 0; p < nnz; ++p) g->uoff[p + 1] += g->uoff[p];
   g->U = (int32_t*)malloc(sizeof(int32_t) * (g->uoff[nnz] + 1));
   if (!g->U) return ORACLE_ENOMEM;
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t u = 0; u < n; ++u)
     for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
       int64_t v = col[p], i = rp[u], j = rp[v], w = g->uoff[p];
@@ -351,11 +381,63 @@ static int setup(G* g, int64_t n, const int64_t* rp, const int32_t* col) {
 
 #define TE(p) ((uint64_t)(g.uoff[(p) + 1] - g.uoff[(p)]))
 
+/* Scratch of one thread: marks and counters over the vertices, and the
+ * thread's partial sums.  The serial build has exactly one. */
+typedef struct {
+  int64_t *cnt, *cc, *wp, *stamp, *stamp2, *stamp3, *touched, *pos;
+  u128 S[S_COUNT];
+} Work;
+
+static void free_work(Work* w, int nw) {
+  if (!w) return;
+  for (int t = 0; t < nw; ++t) {
+    free(w[t].cnt); free(w[t].cc); free(w[t].wp); free(w[t].stamp);
+    free(w[t].stamp2); free(w[t].stamp3); free(w[t].touched); free(w[t].pos);
+  }
+  free(w);
+}
+
+static Work* alloc_work(int nw, int64_t n) {
+  Work* w = (Work*)calloc((size_t)nw, sizeof(Work));
+  if (!w) return NULL;
+  for (int t = 0; t < nw; ++t) {
+    w[t].cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));     /* W(i, .) */
+    w[t].cc = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));      /* cc(i, .) */
+    w[t].wp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));      /* w'(i, .) */
+    w[t].stamp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    w[t].stamp2 = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    w[t].stamp3 = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    w[t].touched = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    w[t].pos = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    if (!w[t].cnt || !w[t].cc || !w[t].wp || !w[t].stamp || !w[t].stamp2 || !w[t].stamp3 ||
+        !w[t].touched || !w[t].pos) { free_work(w, nw); return NULL; }
+    for (int64_t v = 0; v <= n; ++v) { w[t].stamp[v] = -1; w[t].stamp2[v] = -1; w[t].stamp3[v] = -1; }
+  }
+  return w;
+}
+
+/* Add every thread's partial sums to S, in thread order, and clear them. */
+static void fold(u128* S, Work* w, int nw) {
+  for (int t = 0; t < nw; ++t)
+    for (int s = 0; s < S_COUNT; ++s) { S[s] = add(S[s], w[t].S[s]); w[t].S[s] = 0; }
+}
+
+static void reset_marks(Work* w, int nw, int64_t n) {
+  for (int t = 0; t < nw; ++t)
+    for (int64_t v = 0; v <= n; ++v) { w[t].stamp[v] = -1; w[t].stamp2[v] = -1; }
+}
+
 /*
  * Per-element outputs (any may be NULL), indexed like the input:
  *   Te[p], C4e[p], K4e[p] per CSR slot p (both slots of an edge agree);
  *   ti[v], C4i[v], K4i[v] per vertex.
  * sums: S_COUNT entries of two u64 words (lo, hi) each.
+ *
+ * Built with -fopenmp, each loop over a vertex (or over the rows of the
+ * edges) runs its iterations on several threads: every iteration writes only
+ * its own per-element entries and its thread's scratch and partial sums, and
+ * the partial sums are added in thread order.  The arithmetic is the same as
+ * in the serial build; only the order of the exact additions differs.
  */
 int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_t* sums,
                        uint64_t* Te_out, uint64_t* ti_out, uint64_t* C4e_out, uint64_t* C4i_out,
@@ -369,25 +451,17 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
   int64_t nnz = n > 0 ? rp[n] : 0;
   u128 S[S_COUNT];
   memset(S, 0, sizeof(S));
+  const int nw = oracle_num_threads();
 
   uint64_t* t = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
   uint64_t* C4e = (uint64_t*)calloc((size_t)nnz + 1, sizeof(uint64_t));
   uint64_t* C4i = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
   uint64_t* K4e = (uint64_t*)calloc((size_t)nnz + 1, sizeof(uint64_t));
   uint64_t* K4i = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
-  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));   /* W(i, .) */
-  int64_t* cc = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));    /* cc(i, .) */
-  int64_t* wp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));    /* w'(i, .) */
-  int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
-  int64_t* stamp2 = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
-  int64_t* touched = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
-  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
-  int64_t *outp = NULL, *stamp3 = NULL;
+  Work* work = alloc_work(nw, n);
+  int64_t* outp = NULL;
   int32_t* outc = NULL;
-  if (!t || !C4e || !C4i || !K4e || !K4i || !cnt || !cc || !wp || !stamp || !stamp2 || !touched || !pos) {
-    rc = ORACLE_ENOMEM; goto done;
-  }
-  for (int64_t v = 0; v <= n; ++v) { stamp[v] = -1; stamp2[v] = -1; }
+  if (!t || !C4e || !C4i || !K4e || !K4i || !work) { rc = ORACLE_ENOMEM; goto done; }
 
   /* ---- degrees, wedges, stars (Thm 4) ---- */
   S[S_N] = (u128)n;
@@ -446,24 +520,31 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
    * id) and x in U(u,v), the triangle {u, v, x} lies in |U(u,v) cap U(u,x)|
    * 4-cliques (its common neighbours); K4(e) is half the sum over x (Thm 7).
    * U(u,v) is marked in `stamp` so each intersection is one scan of U(u,x). */
-  for (int64_t u = 0; u < n; ++u)
-    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
-      int64_t v = col[p];
-      if (v < u) continue;
-      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) stamp[g.U[q]] = p;
-      uint64_t s = 0;
-      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
-        int64_t x = g.U[q];
-        int64_t px = slot_of(&g, u, x);
-        uint64_t k4t = 0;
-        for (int64_t r = g.uoff[px]; r < g.uoff[px + 1]; ++r) k4t += (stamp[g.U[r]] == p);
-        s += k4t;
-        if (v < x) S[S_N20] = add(S[S_N20], ch2(k4t));       /* each triangle once: N20 (Thm 10) */
+#pragma omp parallel
+  {
+    Work* w = &work[thread_id()];
+    int64_t* stamp = w->stamp;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t u = 0; u < n; ++u)
+      for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+        int64_t v = col[p];
+        if (v < u) continue;
+        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) stamp[g.U[q]] = p;
+        uint64_t s = 0;
+        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+          int64_t x = g.U[q];
+          int64_t px = slot_of(&g, u, x);
+          uint64_t k4t = 0;
+          for (int64_t r = g.uoff[px]; r < g.uoff[px + 1]; ++r) k4t += (stamp[g.U[r]] == p);
+          s += k4t;
+          if (v < x) w->S[S_N20] = add(w->S[S_N20], ch2(k4t));   /* each triangle once: N20 (Thm 10) */
+        }
+        K4e[p] = s / 2;
+        K4e[g.rev[p]] = s / 2;
       }
-      K4e[p] = s / 2;
-      K4e[g.rev[p]] = s / 2;
-    }
-  for (int64_t v = 0; v <= n; ++v) stamp[v] = -1;
+  }
+  fold(S, work, nw);
+  reset_marks(work, nw, n);
   for (int64_t i = 0; i < n; ++i) {
     uint64_t s = 0;
     for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += K4e[p];
@@ -474,27 +555,33 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
 
   /* ---- per-triangle sums N10, N16 (Thm 10) and the directed tailed-triangle
    * correction of the 5-cycle count: each triangle once (u < v < x by id) ---- */
-  for (int64_t u = 0; u < n; ++u)
-    for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
-      int64_t v = col[p];
-      if (v <= u) continue;
-      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
-        int64_t x = g.U[q];
-        if (x <= v) continue;
-        int64_t vs[3] = {u, v, x};
-        uint64_t T_uv = TE(p), T_ux = TE(slot_of(&g, u, x)), T_vx = TE(slot_of(&g, v, x));
-        /* edge opposite vertex k: k = x -> (u,v), k = v -> (u,x), k = u -> (v,x) */
-        uint64_t Topp[3] = {T_vx, T_ux, T_uv};
-        for (int k = 0; k < 3; ++k) {
-          uint64_t dk = (uint64_t)g.deg[vs[k]];
-          S[S_N10A] = add(S[S_N10A], mul(Topp[k] - 1, dk - 2));
+#pragma omp parallel
+  {
+    Work* w = &work[thread_id()];
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t u = 0; u < n; ++u)
+      for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+        int64_t v = col[p];
+        if (v <= u) continue;
+        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+          int64_t x = g.U[q];
+          if (x <= v) continue;
+          int64_t vs[3] = {u, v, x};
+          uint64_t T_uv = TE(p), T_ux = TE(slot_of(&g, u, x)), T_vx = TE(slot_of(&g, v, x));
+          /* edge opposite vertex k: k = x -> (u,v), k = v -> (u,x), k = u -> (v,x) */
+          uint64_t Topp[3] = {T_vx, T_ux, T_uv};
+          for (int k = 0; k < 3; ++k) {
+            uint64_t dk = (uint64_t)g.deg[vs[k]];
+            w->S[S_N10A] = add(w->S[S_N10A], mul(Topp[k] - 1, dk - 2));
+          }
+          /* shared vertex i: the two triangle edges at i */
+          w->S[S_N16A] = add(w->S[S_N16A], mul(T_uv - 1, T_ux - 1));   /* at u */
+          w->S[S_N16A] = add(w->S[S_N16A], mul(T_uv - 1, T_vx - 1));   /* at v */
+          w->S[S_N16A] = add(w->S[S_N16A], mul(T_ux - 1, T_vx - 1));   /* at x */
         }
-        /* shared vertex i: the two triangle edges at i */
-        S[S_N16A] = add(S[S_N16A], mul(T_uv - 1, T_ux - 1));   /* at u */
-        S[S_N16A] = add(S[S_N16A], mul(T_uv - 1, T_vx - 1));   /* at v */
-        S[S_N16A] = add(S[S_N16A], mul(T_ux - 1, T_vx - 1));   /* at x */
       }
-    }
+  }
+  fold(S, work, nw);
 
   /* ---- 4-cycles per vertex and per edge from the pair counts
    * W(i, j) = |N(i) cap N(j)| (two-hop from each i):
@@ -503,51 +590,58 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
    * and, on the same pass, N13 = sum_{i<j} C(W(i,j), 3) and
    * N17 = sum_{i<j} (W(i,j) - 2) cc(i,j) with cc(i,j) the number of edges
    * inside N(i) cap N(j) (Thm 11), gathered from the triangles at i. ---- */
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t nt = 0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      int64_t c = col[p];
-      for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
-        int64_t j = col[q];
-        if (j == i) continue;
-        if (stamp[j] != i) { stamp[j] = i; cnt[j] = 0; cc[j] = 0; touched[nt++] = j; }
-        cnt[j]++;
-      }
-    }
-    /* diamonds with tip i: triangle (i, x, y), x < y, and j in N(x) cap N(y), j != i */
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      int64_t x = col[p];
-      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
-        int64_t y = g.U[q];
-        if (y <= x) continue;
-        int64_t pxy = slot_of(&g, x, y);
-        for (int64_t r = g.uoff[pxy]; r < g.uoff[pxy + 1]; ++r) {
-          int64_t j = g.U[r];
-          if (j != i) cc[j]++;
+#pragma omp parallel
+  {
+    Work* w = &work[thread_id()];
+    int64_t *stamp = w->stamp, *cnt = w->cnt, *cc = w->cc, *touched = w->touched;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t nt = 0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t c = col[p];
+        for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
+          int64_t j = col[q];
+          if (j == i) continue;
+          if (stamp[j] != i) { stamp[j] = i; cnt[j] = 0; cc[j] = 0; touched[nt++] = j; }
+          cnt[j]++;
         }
       }
-    }
-    u128 c4 = 0;
-    for (int64_t a = 0; a < nt; ++a) {
-      int64_t j = touched[a];
-      c4 = add(c4, ch2((uint64_t)cnt[j]));
-      if (j > i) {
-        S[S_N13] = add(S[S_N13], ch3((uint64_t)cnt[j]));
-        if (cc[j]) S[S_N17] = add(S[S_N17], mul((uint64_t)(cnt[j] - 2), (uint64_t)cc[j]));
+      /* diamonds with tip i: triangle (i, x, y), x < y, and j in N(x) cap N(y), j != i */
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t x = col[p];
+        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+          int64_t y = g.U[q];
+          if (y <= x) continue;
+          int64_t pxy = slot_of(&g, x, y);
+          for (int64_t r = g.uoff[pxy]; r < g.uoff[pxy + 1]; ++r) {
+            int64_t j = g.U[r];
+            if (j != i) cc[j]++;
+          }
+        }
       }
-    }
-    C4i[i] = (uint64_t)c4;
-    if (c4 >> 64) g_ovf = 1;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      int64_t k = col[p];
-      uint64_t s = 0;
-      for (int64_t q = rp[k]; q < rp[k + 1]; ++q) {
-        int64_t j = col[q];
-        if (j != i) s += (uint64_t)(cnt[j] - 1);
+      u128 c4 = 0;
+      for (int64_t a = 0; a < nt; ++a) {
+        int64_t j = touched[a];
+        c4 = add(c4, ch2((uint64_t)cnt[j]));
+        if (j > i) {
+          w->S[S_N13] = add(w->S[S_N13], ch3((uint64_t)cnt[j]));
+          if (cc[j]) w->S[S_N17] = add(w->S[S_N17], mul((uint64_t)(cnt[j] - 2), (uint64_t)cc[j]));
+        }
       }
-      C4e[p] = s;
+      C4i[i] = (uint64_t)c4;
+      if (c4 >> 64) set_ovf();
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t k = col[p];
+        uint64_t s = 0;
+        for (int64_t q = rp[k]; q < rp[k + 1]; ++q) {
+          int64_t j = col[q];
+          if (j != i) s += (uint64_t)(cnt[j] - 1);
+        }
+        C4e[p] = s;
+      }
     }
   }
+  fold(S, work, nw);
   for (int64_t i = 0; i < n; ++i) S[S_C4] = add(S[S_C4], C4i[i]);
   S[S_C4] /= 4;
 
@@ -569,23 +663,30 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
    * reaches v through k in N(c) cap N(u) = U(c,u) and v in U(c,k); every
    * 4-cycle is reached from each of its 4 vertices, so the sum of C(., 2)
    * over ordered (u, v) is 4 x N18 (Thm 11). ---- */
-  for (int64_t c = 0; c < n; ++c) {
-    for (int64_t p = rp[c]; p < rp[c + 1]; ++p) pos[col[p]] = p;   /* slot of (c -> x) */
-    for (int64_t p = rp[c]; p < rp[c + 1]; ++p) {
-      int64_t u = col[p], nt = 0;
-      for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
-        int64_t k = g.U[q];
-        int64_t pk = pos[k];
-        for (int64_t r = g.uoff[pk]; r < g.uoff[pk + 1]; ++r) {
-          int64_t v = g.U[r];
-          if (v == u) continue;
-          if (stamp2[v] != p) { stamp2[v] = p; cnt[v] = 0; touched[nt++] = v; }
-          cnt[v]++;
+#pragma omp parallel
+  {
+    Work* w = &work[thread_id()];
+    int64_t *stamp2 = w->stamp2, *cnt = w->cnt, *touched = w->touched, *pos = w->pos;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t c = 0; c < n; ++c) {
+      for (int64_t p = rp[c]; p < rp[c + 1]; ++p) pos[col[p]] = p;   /* slot of (c -> x) */
+      for (int64_t p = rp[c]; p < rp[c + 1]; ++p) {
+        int64_t u = col[p], nt = 0;
+        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+          int64_t k = g.U[q];
+          int64_t pk = pos[k];
+          for (int64_t r = g.uoff[pk]; r < g.uoff[pk + 1]; ++r) {
+            int64_t v = g.U[r];
+            if (v == u) continue;
+            if (stamp2[v] != p) { stamp2[v] = p; cnt[v] = 0; touched[nt++] = v; }
+            cnt[v]++;
+          }
         }
+        for (int64_t a = 0; a < nt; ++a) w->S[S_N18X4] = add(w->S[S_N18X4], ch2((uint64_t)cnt[touched[a]]));
       }
-      for (int64_t a = 0; a < nt; ++a) S[S_N18X4] = add(S[S_N18X4], ch2((uint64_t)cnt[touched[a]]));
     }
   }
+  fold(S, work, nw);
 
   /* ---- 5-cycles (Thm 13).  For every directed 3-path i <- a -> b -> j of the
    * degree-ordered DAG (a < i, a < b < j, b != i, j != i), count the vertices
@@ -600,55 +701,65 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
   /* out-lists of the degree-ordered DAG: N+(v) = {u in N(v) : v < u} */
   outp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
   outc = (int32_t*)malloc(sizeof(int32_t) * (nnz / 2 + 1));
-  stamp3 = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
-  if (!outp || !outc || !stamp3) { rc = ORACLE_ENOMEM; goto done; }
+  if (!outp || !outc) { rc = ORACLE_ENOMEM; goto done; }
   outp[0] = 0;
   for (int64_t v = 0; v < n; ++v) {
-    int64_t w = outp[v];
+    int64_t q = outp[v];
     for (int64_t p = rp[v]; p < rp[v + 1]; ++p)
-      if (prec(&g, v, col[p])) outc[w++] = col[p];
-    outp[v + 1] = w;
+      if (prec(&g, v, col[p])) outc[q++] = col[p];
+    outp[v + 1] = q;
   }
-  for (int64_t v = 0; v <= n; ++v) stamp3[v] = -1;
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t nt = 0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      int64_t c = col[p];
-      for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
-        int64_t j = col[q];
-        if (j == i) continue;
-        int64_t top = prec(&g, i, j) ? j : i;
-        if (!prec(&g, c, top)) continue;
-        if (stamp[j] != -2 - i) { stamp[j] = -2 - i; wp[j] = 0; touched[nt++] = j; }
-        wp[j]++;
-      }
-    }
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) stamp2[col[p]] = -2 - i;   /* N(i) marker */
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      int64_t a = col[p];
-      if (!prec(&g, a, i)) continue;
-      for (int64_t q = rp[a]; q < rp[a + 1]; ++q) stamp3[col[q]] = p;       /* N(a) marker */
-      for (int64_t q = outp[a]; q < outp[a + 1]; ++q) {
-        int64_t b = outc[q];
-        if (b == i) continue;
-        uint64_t b_adj_i = (stamp2[b] == -2 - i);
-        for (int64_t r = outp[b]; r < outp[b + 1]; ++r) {
-          int64_t j = outc[r];
+#pragma omp parallel
+  {
+    Work* w = &work[thread_id()];
+    int64_t *stamp = w->stamp, *stamp2 = w->stamp2, *stamp3 = w->stamp3;
+    int64_t *wp = w->wp, *touched = w->touched;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t nt = 0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t c = col[p];
+        for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
+          int64_t j = col[q];
           if (j == i) continue;
-          uint64_t w = (stamp[j] == -2 - i) ? (uint64_t)wp[j] : 0;
-          S[S_N8M] = add(S[S_N8M], w);
-          S[S_N8Z] = add(S[S_N8Z], (uint64_t)(stamp3[j] == p) + b_adj_i);
+          int64_t top = prec(&g, i, j) ? j : i;
+          if (!prec(&g, c, top)) continue;
+          if (stamp[j] != -2 - i) { stamp[j] = -2 - i; wp[j] = 0; touched[nt++] = j; }
+          wp[j]++;
+        }
+      }
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) stamp2[col[p]] = -2 - i;   /* N(i) marker */
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t a = col[p];
+        if (!prec(&g, a, i)) continue;
+        for (int64_t q = rp[a]; q < rp[a + 1]; ++q) stamp3[col[q]] = p;       /* N(a) marker */
+        for (int64_t q = outp[a]; q < outp[a + 1]; ++q) {
+          int64_t b = outc[q];
+          if (b == i) continue;
+          uint64_t b_adj_i = (stamp2[b] == -2 - i);
+          for (int64_t r = outp[b]; r < outp[b + 1]; ++r) {
+            int64_t j = outc[r];
+            if (j == i) continue;
+            uint64_t wv = (stamp[j] == -2 - i) ? (uint64_t)wp[j] : 0;
+            w->S[S_N8M] = add(w->S[S_N8M], wv);
+            w->S[S_N8Z] = add(w->S[S_N8Z], (uint64_t)(stamp3[j] == p) + b_adj_i);
+          }
         }
       }
     }
   }
+  fold(S, work, nw);
 
   /* ---- 5-cliques (Thm 14): every K5 contains exactly one directed
    * bipyramid whose triangle (i < j < k) is its three lowest vertices; count
    * adjacent pairs inside L = N+(i) cap N+(j) cap N+(k). ---- */
-  for (int64_t v = 0; v <= n; ++v) { stamp[v] = -1; stamp2[v] = -1; }
+  reset_marks(work, nw, n);
+#pragma omp parallel
   {
+    Work* w = &work[thread_id()];
+    int64_t *stamp = w->stamp, *stamp2 = w->stamp2, *touched = w->touched;
     int64_t tag = 0;
+#pragma omp for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i)
       for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
         int64_t j = col[p];
@@ -666,11 +777,12 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
           for (int64_t a2 = 0; a2 < nl; ++a2) {
             int64_t l = touched[a2];
             for (int64_t r = outp[l]; r < outp[l + 1]; ++r)
-              if (stamp2[outc[r]] == tag) S[S_N21] = add(S[S_N21], 1);          /* l -> l' inside L */
+              if (stamp2[outc[r]] == tag) w->S[S_N21] = add(w->S[S_N21], 1);    /* l -> l' inside L */
           }
         }
       }
   }
+  fold(S, work, nw);
 
   /* ---- terms of the disconnected patterns (Thm 3, App. A) ---- */
   S[S_WM] = mul(S[S_W], S[S_M]);
@@ -700,8 +812,8 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
   }
   rc = g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
 done:
-  free(t); free(C4e); free(C4i); free(K4e); free(K4i); free(cnt); free(cc); free(wp);
-  free(stamp); free(stamp2); free(touched); free(pos); free(outp); free(outc); free(stamp3);
+  free(t); free(C4e); free(C4i); free(K4e); free(K4i); free(outp); free(outc);
+  free_work(work, nw);
   free_g(&g);
   return rc;
 }

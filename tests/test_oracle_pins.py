@@ -267,3 +267,19 @@ def test_single_element_definitions_match_full_census():
     v = oracle.vertex_elements(g, vs)
     for k in ("t_i", "C4_i"):
         assert np.array_equal(v[k], pe[k][vs]), k
+
+
+# ----------------------------------------------------------------- OpenMP build
+
+def test_parallel_build_equals_brute_force_and_serial():
+    """The OpenMP build of the same oracle source (used to write the stored
+    results of the large workloads) gives brute force's counts and the serial
+    build's sums and per-element arrays on every brute-force graph."""
+    for g in _graphs_small() + [gg.erdos_renyi(40, 0.15, 8), gg.chung_lu(3000, 2.1, 8, 300, 5)]:
+        par = oracle.census(g, per_element=True, parallel=True)
+        ser = oracle.census(g, per_element=True)
+        assert par["sums"] == ser["sums"], g.name
+        for k in ser["per_element"]:
+            assert np.array_equal(par["per_element"][k], ser["per_element"][k]), (g.name, k)
+        if g.n <= 40:
+            assert par["c5"] == oracle.brute_census(g)["c5"], g.name

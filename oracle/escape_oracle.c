@@ -296,9 +296,11 @@ typedef struct {
   const int64_t* rp;
   const int32_t* col;
   int64_t* deg;
-  /* full common-neighbour list of every CSR slot p = (u -> v):
-   * U[uoff[p] .. uoff[p+1]) = N(u) cap N(v), sorted */
-  int64_t* uoff;
+  /* common-neighbour list of every CSR slot p = (u -> v):
+   * U[ubeg[p] .. ubeg[p] + ulen[p]) = N(u) cap N(v), sorted; the two slots
+   * of an edge share one stored list */
+  int64_t* ubeg;
+  int64_t* ulen;
   int32_t* U;
   int64_t* rev;   /* rev[p] = slot of (v -> u) */
 } G;
@@ -343,34 +345,42 @@ static int validate(int64_t n, const int64_t* rp, const int32_t* col) {
   return bad ? ORACLE_EINVAL : ORACLE_OK;
 }
 
-static void free_g(G* g) { free(g->deg); free(g->uoff); free(g->U); free(g->rev); }
+static void free_g(G* g) { free(g->deg); free(g->ubeg); free(g->ulen); free(g->U); free(g->rev); }
 
 static int setup(G* g, int64_t n, const int64_t* rp, const int32_t* col) {
   memset(g, 0, sizeof(*g));
   g->n = n; g->rp = rp; g->col = col;
   int64_t nnz = n > 0 ? rp[n] : 0;
   g->deg = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
-  g->uoff = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
+  g->ubeg = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
+  g->ulen = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
   g->rev = (int64_t*)malloc(sizeof(int64_t) * (nnz + 1));
-  if (!g->deg || !g->uoff || !g->rev) return ORACLE_ENOMEM;
+  if (!g->deg || !g->ubeg || !g->ulen || !g->rev) return ORACLE_ENOMEM;
   for (int64_t u = 0; u < n; ++u) g->deg[u] = rp[u + 1] - rp[u];
-  /* T(e) = |N(u) cap N(v)| for every slot (list offsets by a prefix sum),
-   * then the lists themselves */
-  g->uoff[0] = 0;
+  /* T(e) = |N(u) cap N(v)| for every slot; the list of an edge is stored
+   * once, at the slot whose row has the smaller id, and the reverse slot
+   * points at it */
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t u = 0; u < n; ++u)
     for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
       int64_t v = col[p];
-      g->uoff[p + 1] = merge_count(col + rp[u], g->deg[u], col + rp[v], g->deg[v]);
+      g->ulen[p] = merge_count(col + rp[u], g->deg[u], col + rp[v], g->deg[v]);
       g->rev[p] = slot_of(g, v, u);
     }
-  for (int64_t p = 0; p < nnz; ++p) g->uoff[p + 1] += g->uoff[p];
-  g->U = (int32_t*)malloc(sizeof(int32_t) * (g->uoff[nnz] + 1));
+  int64_t total = 0;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p)
+      if (u < col[p]) { g->ubeg[p] = total; total += g->ulen[p]; }
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = rp[u]; p < rp[u + 1]; ++p)
+      if (u > col[p]) g->ubeg[p] = g->ubeg[g->rev[p]];
+  g->U = (int32_t*)malloc(sizeof(int32_t) * (total + 1));
   if (!g->U) return ORACLE_ENOMEM;
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t u = 0; u < n; ++u)
     for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
-      int64_t v = col[p], i = rp[u], j = rp[v], w = g->uoff[p];
+      int64_t v = col[p], i = rp[u], j = rp[v], w = g->ubeg[p];
+      if (v < u) continue;
       while (i < rp[u + 1] && j < rp[v + 1]) {
         if (col[i] < col[j]) ++i; else if (col[i] > col[j]) ++j;
         else { g->U[w++] = col[i]; ++i; ++j; }
@@ -379,7 +389,9 @@ static int setup(G* g, int64_t n, const int64_t* rp, const int32_t* col) {
   return ORACLE_OK;
 }
 
-#define TE(p) ((uint64_t)(g.uoff[(p) + 1] - g.uoff[(p)]))
+#define TE(p) ((uint64_t)g.ulen[(p)])
+#define UB(p) (g.ubeg[(p)])
+#define UE(p) (g.ubeg[(p)] + g.ulen[(p)])
 
 /* Scratch of one thread: marks and counters over the vertices, and the
  * thread's partial sums.  The serial build has exactly one. */
@@ -529,13 +541,13 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
       for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
         int64_t v = col[p];
         if (v < u) continue;
-        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) stamp[g.U[q]] = p;
+        for (int64_t q = UB(p); q < UE(p); ++q) stamp[g.U[q]] = p;
         uint64_t s = 0;
-        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        for (int64_t q = UB(p); q < UE(p); ++q) {
           int64_t x = g.U[q];
           int64_t px = slot_of(&g, u, x);
           uint64_t k4t = 0;
-          for (int64_t r = g.uoff[px]; r < g.uoff[px + 1]; ++r) k4t += (stamp[g.U[r]] == p);
+          for (int64_t r = UB(px); r < UE(px); ++r) k4t += (stamp[g.U[r]] == p);
           s += k4t;
           if (v < x) w->S[S_N20] = add(w->S[S_N20], ch2(k4t));   /* each triangle once: N20 (Thm 10) */
         }
@@ -563,7 +575,7 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
       for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
         int64_t v = col[p];
         if (v <= u) continue;
-        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        for (int64_t q = UB(p); q < UE(p); ++q) {
           int64_t x = g.U[q];
           if (x <= v) continue;
           int64_t vs[3] = {u, v, x};
@@ -609,11 +621,11 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
       /* diamonds with tip i: triangle (i, x, y), x < y, and j in N(x) cap N(y), j != i */
       for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
         int64_t x = col[p];
-        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        for (int64_t q = UB(p); q < UE(p); ++q) {
           int64_t y = g.U[q];
           if (y <= x) continue;
           int64_t pxy = slot_of(&g, x, y);
-          for (int64_t r = g.uoff[pxy]; r < g.uoff[pxy + 1]; ++r) {
+          for (int64_t r = UB(pxy); r < UE(pxy); ++r) {
             int64_t j = g.U[r];
             if (j != i) cc[j]++;
           }
@@ -672,10 +684,10 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
       for (int64_t p = rp[c]; p < rp[c + 1]; ++p) pos[col[p]] = p;   /* slot of (c -> x) */
       for (int64_t p = rp[c]; p < rp[c + 1]; ++p) {
         int64_t u = col[p], nt = 0;
-        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        for (int64_t q = UB(p); q < UE(p); ++q) {
           int64_t k = g.U[q];
           int64_t pk = pos[k];
-          for (int64_t r = g.uoff[pk]; r < g.uoff[pk + 1]; ++r) {
+          for (int64_t r = UB(pk); r < UE(pk); ++r) {
             int64_t v = g.U[r];
             if (v == u) continue;
             if (stamp2[v] != p) { stamp2[v] = p; cnt[v] = 0; touched[nt++] = v; }
@@ -764,13 +776,13 @@ int oracle_census_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_
       for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
         int64_t j = col[p];
         if (!prec(&g, i, j)) continue;
-        for (int64_t q = g.uoff[p]; q < g.uoff[p + 1]; ++q) {
+        for (int64_t q = UB(p); q < UE(p); ++q) {
           int64_t k = g.U[q];
           if (!prec(&g, j, k)) continue;
           ++tag;
           for (int64_t r = outp[k]; r < outp[k + 1]; ++r) stamp[outc[r]] = tag;   /* N+(k) */
           int64_t nl = 0;
-          for (int64_t r = g.uoff[p]; r < g.uoff[p + 1]; ++r) {
+          for (int64_t r = UB(p); r < UE(p); ++r) {
             int64_t l = g.U[r];
             if (stamp[l] == tag) { touched[nl++] = l; stamp2[l] = tag; }        /* l in L */
           }

@@ -6,9 +6,14 @@ test can tell whether the graph it regenerates is the one the values were
 computed for (and recompute them live if not).
 
     python tests/golden/make_golden.py chung_lu er500 two_hubs
+    python tests/golden/make_golden.py --parallel rmat20 rmat22
+
+--parallel runs the OpenMP build of the same oracle source on OMP_NUM_THREADS
+threads (its equality with the serial build is pinned in test_oracle_pins).
 """
 import json
 import os
+import platform
 import sys
 import time
 
@@ -25,16 +30,20 @@ WORKLOADS = {
     "chung_lu": lambda: gg.config_chung_lu(1),
     "er500": lambda: gg.config_er500(0),
     "two_hubs": lambda: gg.two_hubs(),
+    "rmat20": lambda: gg.config_rmat(20, 1),
+    "rmat22": lambda: gg.config_rmat(22, 1),
 }
 
 
-def write(name):
+def write(name, parallel=False):
     g = WORKLOADS[name]()
     t0 = time.time()
-    c = oracle.census(g)
+    c = oracle.census(g, parallel=parallel)
     out = {
         "workload": name, "graph": g.name, "n": g.n, "m": g.m, "sha256": graph_hash(g),
         "oracle_seconds": round(time.time() - t0, 1),
+        "oracle_threads": oracle.num_threads(parallel),
+        "oracle_host": f"{platform.machine()}, {os.cpu_count()} cores",
         "c3": [str(x) for x in c["c3"]], "c4": [str(x) for x in c["c4"]], "c5": [str(x) for x in c["c5"]],
         "n3": [str(x) for x in c["n3"]], "n4": [str(x) for x in c["n4"]], "n5": [str(x) for x in c["n5"]],
         "sums": {k: str(v) for k, v in c["sums"].items()},
@@ -45,5 +54,7 @@ def write(name):
 
 
 if __name__ == "__main__":
-    for name in sys.argv[1:] or list(WORKLOADS):
-        write(name)
+    par = "--parallel" in sys.argv
+    names = [a for a in sys.argv[1:] if not a.startswith("--")]
+    for name in names or ["chung_lu", "er500", "two_hubs"]:
+        write(name, par)

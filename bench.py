@@ -1,12 +1,16 @@
 """Benchmark: exact 34-class 5-vertex census (plus 3-/4-vertex counts) of one
 synthetic graph per step, in edges per second.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload chung_lu|rmat22|er500|batch|serve]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22|chung_lu|er500|batch|serve]
   python bench.py --impl reference ...     # the CPU oracle, timed on a bounded sample
 
-One step = one escape_census5 call on a graph already resident in HBM (its
-CSR loaded once before timing): orientation, every enumeration kernel and the
-128-bit assembly.  The L2 cache is flushed (256 MB write) between steps.
+The default workload is the R-MAT scale-22 graph (~64.2M edges).  One step =
+one escape_census5 call on a graph already resident in HBM (its CSR loaded
+once before timing): orientation, every enumeration kernel and the 128-bit
+assembly.  The L2 cache is flushed (256 MB write) between steps.  The
+end-to-end figure (host CSR in pinned memory, load + census + result read
+back) is timed over every step, or over three steps when a census takes a
+second or more.
 N > 1 (torchrun) runs independent replicas, one per GPU: the census of one
 graph is not sharded across GPUs (weak scaling, value = all ranks' edges /
 slowest rank's time).  One JSON line is printed by rank 0.
@@ -187,19 +191,55 @@ def stored_traffic(kernel: str, workload: str):
     return None
 
 
-def cpu_baseline(sample_n: int = 32768):
-    """The oracle as it stands, on a bounded sample of the workload: a Chung-Lu
-    graph of the same generator parameters and fewer vertices."""
+# bounded samples of each workload for the oracle's CPU timings: the same
+# generator and parameters at fewer vertices (cpu_baseline: ~10-30 s of one
+# core; reference arm: a few seconds per step)
+SAMPLES = {
+    "chung_lu": {"baseline": ("Chung-Lu n=32768 (exponent 2.1, mean 16, clip 8192, seed 1)",
+                              lambda gg: gg.chung_lu(32768, 2.1, 16.0, 8192.0, 1)),
+                 "reference": ("Chung-Lu n=8192 (exponent 2.1, mean 16, clip 8192, seed 1)",
+                               lambda gg: gg.chung_lu(8192, 2.1, 16.0, 8192.0, 1))},
+    "rmat22": {"baseline": ("R-MAT scale 14, edge factor 16, (0.57,0.19,0.19,0.05), seed 1",
+                            lambda gg: gg.config_rmat(14, 1)),
+               "reference": ("R-MAT scale 12, edge factor 16, (0.57,0.19,0.19,0.05), seed 1",
+                             lambda gg: gg.config_rmat(12, 1))},
+    "er500": {"baseline": ("Erdos-Renyi G(500, 0.012), seed 0", lambda gg: gg.config_er500(0)),
+              "reference": ("Erdos-Renyi G(500, 0.012), seed 0", lambda gg: gg.config_er500(0))},
+}
+
+
+def stored_oracle_run(name: str):
+    """Wall time, thread count and host of the stored oracle result of the full
+    workload graph (tests/golden), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"census_{name}.json")
+    try:
+        with open(path) as f:
+            gold = json.load(f)
+        return {"seconds": gold["oracle_seconds"], "threads": gold.get("oracle_threads", 1),
+                "host": gold.get("oracle_host", "the build container"), "m": gold["m"]}
+    except Exception:
+        return None
+
+
+def cpu_baseline(workload: str):
+    """The oracle as it stands (serial build), on a bounded sample of the
+    workload, plus the stored full-graph oracle run for comparison."""
     import graphgen as gg
     import oracle
-    g = gg.chung_lu(sample_n, 2.1, 16.0, 8192.0, 1)
+    desc, make = SAMPLES.get(workload, SAMPLES["chung_lu"])["baseline"]
+    g = make(gg)
     oracle.build()
     t0 = time.perf_counter()
     oracle.census(g)
     dt = time.perf_counter() - t0
-    return {"value": g.m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Chung-Lu n={sample_n} (exponent 2.1, mean 16, clip 8192, seed 1), m={g.m}, full census, "
-                      f"{dt:.1f} s single-threaded"}
+    out = {"value": g.m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{desc}, m={g.m}, full census, {dt:.1f} s on one core"}
+    full = stored_oracle_run(workload)
+    if full:
+        out["full_graph"] = {"value": full["m"] / full["seconds"], "unit": UNIT, "seconds": full["seconds"],
+                             "threads": full["threads"], "host": full["host"],
+                             "note": "the stored oracle result of the whole workload graph (tests/golden)"}
+    return out
 
 
 def run_reference(args):
@@ -209,8 +249,8 @@ def run_reference(args):
     import graphgen as gg
     import oracle
     oracle.build()
-    sample_n = 8192
-    g = gg.chung_lu(sample_n, 2.1, 16.0, 8192.0, 1)
+    desc, make = SAMPLES.get(args.workload, SAMPLES["chung_lu"])["reference"]
+    g = make(gg)
     for _ in range(args.warmup):
         oracle.census(g)
     t0 = time.perf_counter()
@@ -222,12 +262,39 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "sample": f"Chung-Lu n={sample_n} per step"},
+        "config": {"workload": WORKLOADS[args.workload], "sample": f"{desc} per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"Chung-Lu n={sample_n} (same generator), m={g.m}, full census per step"},
+                         "sample": f"{desc}, m={g.m}, full census per step (serial oracle build)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def census_alg_bytes(g, sums):
+    """Algorithmic bytes of the whole census, 4 B per vertex id the method must
+    read plus 8 B per count-array entry: the orientation (2m), the triangle
+    intersections (sum over oriented edges u->v of d+(u) + d+(v)), both 4-cycle
+    passes (2 (W++ + W+-)), the pair sweep (W), the cc and wheel sweeps (2D)
+    and the directed 3-paths of the 5-cycle count (DP), with W and D from the
+    stored oracle result and the rest from the degree-ordered DAG.  The 4-clique
+    and bipyramid terms need per-triangle counts that are not stored, so this
+    is a lower bound of the full formula."""
+    import numpy as np
+    deg = g.degrees().astype(np.int64)
+    n = g.n
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dst = g.col.astype(np.int64)
+    up = (deg[src] < deg[dst]) | ((deg[src] == deg[dst]) & (src < dst))      # src precedes dst
+    dplus = np.bincount(src[up], minlength=n).astype(np.int64)
+    dminus = deg - dplus
+    wpp = int((dplus * (dplus - 1) // 2).sum())
+    wpm = int((dplus * dminus).sum())
+    tri = int((dplus[src[up]] + dplus[dst[up]]).sum())
+    dp = int(((dplus[src[up]] - 1) * dplus[dst[up]]).sum())                 # i <- a -> b -> j
+    terms = {"orient": 2 * g.m, "triangles": tri, "cycles4": 2 * (wpp + wpm), "pairs": sums["W"],
+             "cc_wheels": 2 * sums["D"], "paths3": dp}
+    total = 4 * sum(terms.values()) + 8 * (n + 3 * g.m)
+    return total, {k: int(v) for k, v in terms.items()}
 
 
 def slowest_rank_ms(total_ms: float, world: int, device: str) -> float:
@@ -365,7 +432,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chung_lu", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=1000, help="graphs in the batch workload (config: 10000)")
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -447,7 +514,9 @@ def main():
     h2d = int(g.row_ptr.nbytes + g.col.nbytes)
     d2h = 2 * 49 * 16
     e2e_ms = 0.0
-    for _ in range(args.steps):
+    # graphs of a second or more per census: a few end-to-end steps suffice
+    e2e_steps = args.steps if ms_per_step < 1000 else min(args.steps, 3)
+    for _ in range(e2e_steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -456,7 +525,7 @@ def main():
         esc.escape_free(hh)
         e2e_ms += 1000 * (time.perf_counter() - t0)
         assert r2["c5"] == res["c5"]
-    e2e_value = world * g.m / (e2e_ms / args.steps / 1000.0)
+    e2e_value = world * g.m / (e2e_ms / e2e_steps / 1000.0)
     esc.escape_free(h)
 
     if rank != 0:
@@ -491,7 +560,15 @@ def main():
                 "note": "phase_ms is timed with the independent sweeps overlapping on side streams; "
                         "achieved_alone uses the phase's time when every phase runs alone"}
         break
-    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    census_roof = None
+    if sums is not None:
+        b_all, terms = census_alg_bytes(g, sums)
+        ach = b_all / (ms_per_step / 1000.0) / 1e9
+        census_roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "algorithmic_bytes": b_all, "terms": terms,
+                       "bytes_model": "4 B x (2m + sum_{u->v}(d+u + d+v) + 2(W++ + W+-) + W + 2D + DP) + "
+                                      "8 B x (n + 3m); 4-clique and bipyramid terms omitted (lower bound)"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -499,11 +576,13 @@ def main():
         "config": {"workload": WORKLOADS[args.workload], "n": g.n, "m": g.m,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
         "gpu_launches": launches,
         "phase_ms": {k: round(v, 3) for k, v in avg_phase.items()},
         "phase_ms_alone": {k: round(v, 3) for k, v in alone_phase.items()},
         "roofline": roof,
+        "census_roofline": census_roof,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

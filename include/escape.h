@@ -177,17 +177,22 @@ long long escape_last_kernel_launches(const escape_graph* g);
  *   n         number of vertices, 0 <= n <= ESCAPE_NOALLOC_MAX_N, else EOVERFLOW
  *   row_ptr   DEVICE int64[n + 1], col DEVICE int32[row_ptr[n]]: a simple graph
  *             as for escape_load_csr without NORMALIZE (sorted symmetric rows,
- *             no self-loops); ids outside [0, n) are skipped and give EINVAL
+ *             no self-loops); ids outside [0, n), and row offsets outside
+ *             [0, row_ptr[n]] or decreasing, are skipped and give EINVAL
  *   c4_v      DEVICE uint64[n] output: 4-cycles through each vertex
  *   c4_total  DEVICE uint64[1] output: number of 4-cycles
  * Work space is one fixed device array of ESCAPE_NOALLOC_MAX_N x 64 words
- * (8 MiB) inside the library, held by every GPU that loads the library until
- * the process exits, and shared by every call: calls whose GPU work overlaps
- * (on different streams or threads) race and must be serialised by the caller.
- * Each call clears the work space and the outputs before counting.  The first
- * call on a device looks up the array's device address (one-time set-up per
- * device); make that first call before any stream capture.  No cudaMalloc,
- * cudaFree or allocating library routine is called.
+ * (8 MiB) inside the library, shared by every call: calls whose GPU work
+ * overlaps (on different streams or threads) race and must be serialised by
+ * the caller.  Each call clears the work space and the outputs before
+ * counting.  The array takes its device memory when the library's device
+ * code is loaded on a device -- with CUDA's lazy module loading, during the
+ * first call on that device -- and keeps it until the process exits; so make
+ * the first call on each device before the caller's own pool claims the
+ * device's memory.  That first call also looks up the array's device address
+ * (one-time set-up per device); make it before any stream capture.  Every
+ * call reads a status word back and waits for its stream before returning.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
  */
 #define ESCAPE_NOALLOC_MAX_N 32768
 escape_status escape_cycles4_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t* c4_v,

@@ -1587,13 +1587,18 @@ struct DevBuf {
 #define ESC_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return _e; } while (0)
 
 // Side streams for the concurrent phases; events order them after / before
-// the caller's stream.  Destroyed (after the caller's stream has joined them)
-// when the census returns.
+// the caller's stream.  Destroyed when the census returns, after each has
+// drained: on an early error return the caller's stream may not have joined
+// them, and the buffers their kernels use go back to the cache only after
+// this destructor (they are declared before the StreamSet).
 struct StreamSet {
   cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};
   int count = 0;
   ~StreamSet() {
-    for (int i = 0; i < count; ++i) cudaStreamDestroy(st[i]);
+    for (int i = 0; i < count; ++i) {
+      cudaStreamSynchronize(st[i]);
+      cudaStreamDestroy(st[i]);
+    }
   }
   // prio[i] != 0: the device's greatest (most urgent) priority, else its least
   cudaError_t create(int k, const int* urgent) {

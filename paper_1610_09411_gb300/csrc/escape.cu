@@ -234,6 +234,25 @@ __global__ void k_map_vertices(int64_t n, const int32_t* rank, const unsigned lo
   }
 }
 
+// Every row offset of a CSR held in host memory: rp[0] = 0, non-decreasing,
+// rp[rows] = nnz (nnz < 0: only rp[0] = 0 and monotone, nnz taken from the
+// last entry).  Kernels index col through these offsets, so a CSR from device
+// memory is copied here and checked before any kernel sees it.
+bool row_ptr_ok(const int64_t* rp, int64_t rows, int64_t nnz) {
+  if (rp[0] != 0) return false;
+  for (int64_t i = 0; i < rows; ++i)
+    if (rp[i + 1] < rp[i]) return false;
+  return nnz < 0 || rp[rows] == nnz;
+}
+
+// The row offsets of a device-memory CSR, copied to the host (synchronises s).
+cudaError_t fetch_row_ptr(const int64_t* d_rp, int64_t rows, std::vector<int64_t>& h, cudaStream_t s) {
+  h.resize((size_t)rows + 1);
+  cudaError_t e = cudaMemcpyAsync(h.data(), d_rp, sizeof(int64_t) * (rows + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
 escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_col, int64_t n, int64_t nnz,
                          escape_census* out, cudaStream_t s, bool keep, esc::PerElement* pe, esc::Oriented* ori,
                          float* phase_ms, int* nphase, bool four_only = false) {
@@ -312,11 +331,17 @@ escape_status escape_load_csr(int64_t n, int64_t nnz, const int64_t* row_ptr, co
   if (!g) return ESCAPE_ENOMEM;
   cudaGetDevice(&g->device);
   g->sms = device_sms(g->device);
-  // host-side checks of the row pointer (host input) before any copy
-  if (!dev_ptrs && n > 0) {
-    if (row_ptr[0] != 0 || row_ptr[n] != nnz) { delete g; return ESCAPE_EINVAL; }
-    for (int64_t i = 0; i < n; ++i)
-      if (row_ptr[i + 1] < row_ptr[i]) { delete g; return ESCAPE_EINVAL; }
+  // every row offset is checked on the host before any copy or kernel: host
+  // input directly, device input after copying the offsets here
+  if (n > 0) {
+    std::vector<int64_t> hrp;
+    const int64_t* h = row_ptr;
+    if (dev_ptrs) {
+      cudaError_t e0 = fetch_row_ptr(row_ptr, n, hrp, s);
+      if (e0 != cudaSuccess) { delete g; return from_cuda(e0); }
+      h = hrp.data();
+    }
+    if (!row_ptr_ok(h, n, nnz)) { delete g; return ESCAPE_EINVAL; }
   }
   int64_t* d_rp = nullptr;
   int32_t* d_col = nullptr;
@@ -331,14 +356,6 @@ escape_status escape_load_csr(int64_t n, int64_t nnz, const int64_t* row_ptr, co
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, kind, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
   escape_status st = from_cuda(e);
-  if (st == ESCAPE_OK && dev_ptrs && n > 0) {
-    int64_t ends[2];
-    e = cudaMemcpyAsync(&ends[0], d_rp, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], d_rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    st = from_cuda(e);
-    if (st == ESCAPE_OK && (ends[0] != 0 || ends[1] != nnz)) st = ESCAPE_EINVAL;
-  }
   if (st == ESCAPE_OK && (flags & ESCAPE_NORMALIZE)) {
     esc::DeviceArena arena;
     size_t ab = (size_t)(2 * nnz + 16) * 8 * 3 + (size_t)((2 * nnz) / 4096 + 2) * 256 * 8 * 2 + (1 << 22);
@@ -449,20 +466,17 @@ escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offset
     if (voff[k + 1] < voff[k] || voff[k + 1] - voff[k] > 2147483647LL) return ESCAPE_EINVAL;
   int64_t rows = voff[num_graphs];
   if (rows > 2147483647LL) return ESCAPE_EOVERFLOW;      // the union is one graph of int32 ids
-  int64_t ends[2] = {0, 0};
+  // every row offset is checked on the host before any kernel indexes col
+  // through it (device input is copied here first)
+  std::vector<int64_t> hrp;
+  const int64_t* h = row_ptr;
   if (dev_ptrs) {
-    e = cudaMemcpyAsync(&ends[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    e = fetch_row_ptr(row_ptr, rows, hrp, s);
     if (e != cudaSuccess) return from_cuda(e);
-  } else {
-    ends[0] = row_ptr[0];
-    ends[1] = row_ptr[rows];
-    for (int64_t r = 0; r < rows; ++r)
-      if (row_ptr[r + 1] < row_ptr[r]) return ESCAPE_EINVAL;
+    h = hrp.data();
   }
-  if (ends[0] != 0 || ends[1] < 0) return ESCAPE_EINVAL;
-  int64_t nnz = ends[1];
+  if (!row_ptr_ok(h, rows, -1)) return ESCAPE_EINVAL;
+  int64_t nnz = h[rows];
   if (nnz > 0 && !col) return ESCAPE_EINVAL;
   // device copies: offsets, rows, entries turned into union ids
   int64_t *d_voff = nullptr, *d_rp = nullptr;

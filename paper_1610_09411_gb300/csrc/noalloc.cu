@@ -36,6 +36,20 @@ __device__ __forceinline__ bool na_prec(const int64_t* rp, int64_t a, int64_t b)
   return da < db || (da == db && a < b);
 }
 
+// Row v's entry range, clamped: an offset outside [0, rp[n]] or a row that
+// ends before it starts sets the status word and reads as an empty row, so no
+// access leaves col[0 .. rp[n]).
+__device__ __forceinline__ void na_row(const int64_t* rp, int64_t n, int64_t v, int64_t& b, int64_t& e,
+                                       unsigned int* status) {
+  b = rp[v];
+  e = rp[v + 1];
+  int64_t lim = rp[n];
+  if (b < 0 || e < b || e > lim) {
+    atomicOr(status, 1u);
+    b = e = 0;
+  }
+}
+
 __global__ void k_cycles4_noalloc(const int64_t* rp, const int32_t* col, int64_t n, unsigned int* scratch,
                                   unsigned long long* c4v, unsigned long long* c4_total) {
   __shared__ u128 sh[32];
@@ -56,12 +70,16 @@ __global__ void k_cycles4_noalloc(const int64_t* rp, const int32_t* col, int64_t
     if (i >= n) break;
     if (threadIdx.x == 0) nt = 0;
     __syncthreads();
+    int64_t ib, ie;
+    na_row(rp, n, i, ib, ie, status);
     // pass 1: wedges i - k - j with k, j below i in the degree order
-    for (int64_t p = rp[i] + wid; p < rp[i + 1]; p += nw) {
+    for (int64_t p = ib + wid; p < ie; p += nw) {
       int32_t k = col[p];
       if (k < 0 || k >= n) { if (lane == 0) atomicOr(status, 1u); continue; }
       if (!na_prec(rp, k, i)) continue;
-      for (int64_t q = rp[k] + lane; q < rp[k + 1]; q += 32) {
+      int64_t kb, ke;
+      na_row(rp, n, k, kb, ke, status);
+      for (int64_t q = kb + lane; q < ke; q += 32) {
         int32_t j = col[q];
         if (j < 0 || j >= n) { atomicOr(status, 1u); continue; }
         if (j == i || !na_prec(rp, j, i)) continue;
@@ -80,11 +98,13 @@ __global__ void k_cycles4_noalloc(const int64_t* rp, const int32_t* col, int64_t
     u128 s = block_sum_u128(mine, sh);
     if (threadIdx.x == 0) { if (s) atomicAdd(&c4v[i], (unsigned long long)s); total += s; }
     // pass 3: w - 1 to every middle k
-    for (int64_t p = rp[i] + wid; p < rp[i + 1]; p += nw) {
+    for (int64_t p = ib + wid; p < ie; p += nw) {
       int32_t k = col[p];
       if (k < 0 || k >= n || !na_prec(rp, k, i)) continue;
       unsigned long long sk = 0;
-      for (int64_t q = rp[k] + lane; q < rp[k + 1]; q += 32) {
+      int64_t kb, ke;
+      na_row(rp, n, k, kb, ke, status);
+      for (int64_t q = kb + lane; q < ke; q += 32) {
         int32_t j = col[q];
         if (j < 0 || j >= n || j == i || !na_prec(rp, j, i)) continue;
         sk += w[j] - 1;

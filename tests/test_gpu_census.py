@@ -285,6 +285,30 @@ def test_invalid_inputs_rejected(case):
     assert ei.value.code == 1
 
 
+@pytest.mark.parametrize("bad", [[0, 4, 2, 6], [0, 9, 4, 6], [0, 2, 9, 6], [0, -2, 4, 6], [0, 2, 4, 5]],
+                         ids=["decreasing", "interior_past_nnz", "interior_past_nnz_late", "negative", "end_not_nnz"])
+def test_device_row_ptr_checked_on_the_host(bad):
+    """Device-memory CSRs: every row offset is copied to the host and checked
+    before any kernel indexes col through it, so a malformed row pointer is
+    EINVAL for both escape_load_csr and escape_census5_batch."""
+    import torch
+    from paper_1610_09411_gb300 import escape as esc
+    col = torch.tensor([1, 2, 0, 2, 0, 1], dtype=torch.int32, device="cuda")    # a triangle
+    rp = torch.tensor(bad, dtype=torch.int64, device="cuda")
+    with pytest.raises(esc.EscapeError) as ei:
+        esc.escape_load_csr(3, rp, col)
+    assert ei.value.code == 1
+    if bad[-1] == 6:        # the batch takes its entry count from the last offset
+        voff = torch.tensor([0, 3], dtype=torch.int64, device="cuda")
+        with pytest.raises(esc.EscapeError) as ei:
+            esc.escape_census5_batch(voff, rp, col)
+        assert ei.value.code == 1
+    # the library is still usable
+    good = torch.tensor([0, 2, 4, 6], dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    assert esc.census(good, col, n=3)["c3"][3] == 1
+
+
 def test_batch_matches_single_graph_calls():
     from paper_1610_09411_gb300 import escape as esc
     graphs = gg.batch_graphs(12, 5, n_lo=20, n_hi=300)

@@ -2,14 +2,16 @@
 library (for callers that cannot allocate device memory when they count).
 
 Checked through the C ABI against the existing census entry point
-(escape_census5 + escape_per_element), on two calls in a row so that the
-shared fixed work space is shown to start clean each time.  Collected last on
-purpose; it must also pass alone in a fresh process.
+(escape_census5 + escape_per_element) and against the CPU oracle, on two
+calls in a row so that the shared fixed work space is shown to start clean
+each time, and with the device's free memory unchanged across the second
+call.  Collected last on purpose; it must also pass alone in a fresh process.
 """
 import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -42,12 +44,19 @@ def test_noalloc_matches_census_on_two_calls(make):
     from paper_1610_09411_gb300 import escape as esc
     g = make()
     want_v, want_total = _reference(g)
+    o = oracle.census(g, per_element=True)
+    assert np.array_equal(o["per_element"]["C4_i"], want_v) and o["n4"][3] == want_total
     rp = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
-    for _ in range(2):
+    for call in range(2):
         c4_v = torch.full((g.n,), 7, dtype=torch.int64, device="cuda")     # garbage on purpose
         total = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         esc.escape_cycles4_noalloc(g.n, rp, col, c4_v, total)
+        free_after = torch.cuda.mem_get_info()[0]
+        if call == 1:       # the first call on a device may load the module that holds the array
+            assert free_after == free_before
         assert np.array_equal(c4_v.cpu().numpy().astype(np.uint64), want_v)
         assert int(total.item()) == want_total
 

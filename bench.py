@@ -11,9 +11,12 @@ assembly.  The L2 cache is flushed (256 MB write) between steps.  The
 end-to-end figure (host CSR in pinned memory, load + census + result read
 back) is timed over every step, or over three steps when a census takes a
 second or more.
-N > 1 (torchrun) runs independent replicas, one per GPU: the census of one
-graph is not sharded across GPUs (weak scaling, value = all ranks' edges /
-slowest rank's time).  One JSON line is printed by rank 0.
+N > 1 (torchrun, NCCL) splits the census of the one graph over the ranks:
+every rank counts the work items it owns (escape_census5_part), the ranks
+add their sums and per-element arrays (the census's one exchange step,
+paper_1610_09411_gb300/shard.py) and finish (strong scaling: value = the
+graph's edges / the slowest rank's time per step).  One JSON line is printed
+by rank 0.
 """
 from __future__ import annotations
 
@@ -150,28 +153,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# the code that decides each swept phase's DRAM traffic: a section of
+# census.cu between two of its banner comments, and the host lines that shape
+# its launches
+DIGEST_SECTIONS = {
+    "k_pairs": ([("// Thm 11/12: N13", "// Thm 11: N18 (wheels)"),
+                 ("struct PairPlan {", "\ncudaError_t run_census(")],
+                ("PAIR_", "PairPlan", "pplan", "plan_pair", "launch_pairs", "k_pairs", "ptasks", "tsB")),
+}
+
+
 def source_digest(kernel: str = "k_pairs") -> str:
-    """Digest of what decides a kernel's DRAM traffic: its function text, the
-    counter struct it uses and every line naming its constants or launch
-    configuration in census.cu.  Host-side edits elsewhere leave it unchanged;
-    any edit of the kernel changes it (and a failed extraction hashes the whole
-    file, which only makes a stored figure look stale)."""
+    """Digest of what decides a kernel's DRAM traffic: the section of
+    census.cu that holds the kernel and its device helpers, the counter struct
+    it uses and every line naming its constants or launch configuration.
+    Edits elsewhere leave it unchanged; any edit of the kernel changes it (and
+    a failed extraction hashes the whole file, which only makes a stored figure
+    look stale)."""
     path = os.path.join(ROOT, "paper_1610_09411_gb300", "csrc", "census.cu")
     with open(path) as f:
         src = f.read()
     h = hashlib.sha256()
-    sig = src.find(f" {kernel}(")
-    start = src.rfind("template", 0, sig) if sig >= 0 else -1
-    end = src.find("\n}\n", sig) if sig >= 0 else -1
-    st = src.find("struct TaggedCounters {")
-    st_end = src.find("\n};\n", st) if st >= 0 else -1
-    if min(sig, start, end, st, st_end) < 0:
-        h.update(src.encode())
-        return h.hexdigest()[:16]
-    h.update(src[start:end].encode())
-    h.update(src[st:st_end].encode())
-    for line in src.splitlines():
-        if any(k in line for k in ("PAIR_ILP", "PAIR_CTAS_PER_SM", "grid_pairs", "pthreads", f"{kernel}<")):
+    spans, keys = DIGEST_SECTIONS.get(kernel, ([(f" {kernel}(", "\n}\n")], (kernel,)))
+    spans = spans + [("struct TaggedCounters {", "\n};\n")]
+    cut = []
+    for begin, end in spans:
+        a = src.find(begin)
+        b = src.find(end, a + 1) if a >= 0 else -1
+        if min(a, b) < 0:
+            h.update(src.encode())
+            return h.hexdigest()[:16]
+        cut.append((a, b))
+    rest, pos = [], 0
+    for a, b in sorted(cut):
+        h.update(src[a:b].encode())
+        rest.append(src[pos:a])
+        pos = max(pos, b)
+    rest.append(src[pos:])
+    for line in "".join(rest).splitlines():
+        if any(k in line for k in keys):
             h.update(line.encode())
     return h.hexdigest()[:16]
 
@@ -298,7 +318,7 @@ def census_alg_bytes(g, sums):
 
 
 def slowest_rank_ms(total_ms: float, world: int, device: str) -> float:
-    """Max over ranks of the timed region (replicas: the job ends with the slowest)."""
+    """Max over ranks of the timed region (the job ends with the slowest rank)."""
     if world <= 1:
         return total_ms
     import torch
@@ -309,9 +329,9 @@ def slowest_rank_ms(total_ms: float, world: int, device: str) -> float:
     return float(t.item())
 
 
-def replica_value(world: int, m: int, ms_per_step: float) -> float:
-    """Whole-job edges/s: every rank counted its own copy of the graph."""
-    return world * m / (ms_per_step / 1000.0)
+def job_value(m: int, ms_per_step: float) -> float:
+    """Whole-job edges/s: the ranks together count one graph of m edges per step."""
+    return m / (ms_per_step / 1000.0)
 
 
 def _pack(graphs):
@@ -462,17 +482,26 @@ def main():
         pbuild.build()
     if world > 1:
         dist.barrier()
-    from paper_1610_09411_gb300 import escape as esc
+    from paper_1610_09411_gb300 import autotune, escape as esc
+    from paper_1610_09411_gb300 import shard
 
     g = make_graph(args.workload)
+    knobs = autotune.apply(g.nnz)               # the tuned launch knobs of the graph's size class
+    cps = autotune.cta_per_sm()
+
+    def census_step(handle):
+        if world == 1:
+            return esc.escape_census5(handle)
+        return shard.sharded_census(handle, g.n, g.nnz)
     stream = torch.cuda.current_stream()
     rp = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
     torch.cuda.synchronize()
     h = esc.escape_load_csr(g.n, rp, col)
+    esc.escape_set_options(h, False, cps, None)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     for _ in range(args.warmup):
-        res = esc.escape_census5(h)
+        res = census_step(h)
 
     sampler = ClockSampler(local) if rank == 0 else None
     phase_tot = {}
@@ -488,24 +517,29 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = esc.escape_census5(h)
+        res = census_step(h)
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
-        for k, v in esc.escape_last_phase_ms(h).items():
-            phase_tot[k] = phase_tot.get(k, 0.0) + v
+        if world == 1:
+            for k, v in esc.escape_last_phase_ms(h).items():
+                phase_tot[k] = phase_tot.get(k, 0.0) + v
         launches += esc.escape_last_kernel_launches(h)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     # outside the timed region: one census with the phases run one after
     # another, for each kernel's duration alone
-    esc.escape_set_options(h, False, 0, True)
-    esc.escape_census5(h)
-    alone_phase = esc.escape_last_phase_ms(h)
-    esc.escape_set_options(h, False, 0, None)
+    alone_phase = {}
+    if world == 1:
+        esc.escape_set_options(h, False, cps, True)
+        esc.escape_census5(h)
+        alone_phase = esc.escape_last_phase_ms(h)
+        esc.escape_set_options(h, False, cps, None)
     total_ms = slowest_rank_ms(total_ms, world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = replica_value(world, g.m, ms_per_step)
+    value = job_value(g.m, ms_per_step)
 
     # end to end through the public C ABI with pinned host buffers: H2D of the
     # CSR, the census, D2H of the result struct, every step
@@ -521,11 +555,13 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hh = esc.escape_load_csr(g.n, hrp.numpy(), hcol.numpy())
-        r2 = esc.escape_census5(hh)
+        esc.escape_set_options(hh, False, cps, None)
+        r2 = census_step(hh)
         esc.escape_free(hh)
         e2e_ms += 1000 * (time.perf_counter() - t0)
         assert r2["c5"] == res["c5"]
-    e2e_value = world * g.m / (e2e_ms / e2e_steps / 1000.0)
+    e2e_ms = slowest_rank_ms(e2e_ms, world, "cuda")
+    e2e_value = g.m / (e2e_ms / e2e_steps / 1000.0)
     esc.escape_free(h)
 
     if rank != 0:
@@ -571,11 +607,13 @@ def main():
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "u128", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "n": g.n, "m": g.m,
                    "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "tuning": knobs or "library defaults",
+                   "parallelism": f"one census split over {world} GPUs (owned items, one exchange)"
+                                  if world > 1 else "1 GPU"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": launches,

@@ -246,19 +246,23 @@ def config_rmat(scale: int = 22, seed: int = 1) -> Graph:
     return rmat(scale, 16, 0.57, 0.19, 0.19, seed)
 
 
+def batch_member(k: int, seed: int, n_lo: int = 20, n_hi: int = 2000,
+                 p_lo: float = 0.01, p_hi: float = 0.3, m_lo: int = 2, m_hi: int = 6) -> Graph:
+    """Graph k of the batch workload (each member is drawn from its own
+    counter-based streams, so any member can be made alone): size uniform in
+    [n_lo, n_hi]; even k G(n, p) with p uniform in [p_lo, p_hi], odd k
+    Barabasi-Albert with m uniform in [m_lo, m_hi]."""
+    n = n_lo + stream_draw(seed, 1, k) % (n_hi - n_lo + 1)
+    gseed = stream_draw(seed, 2, k)
+    if k % 2 == 0:
+        u = (stream_draw(seed, 3, k) >> 11) / float(1 << 53)
+        p = p_lo + (p_hi - p_lo) * u
+        return erdos_renyi(n, p, gseed)
+    m_att = m_lo + stream_draw(seed, 4, k) % (m_hi - m_lo + 1)
+    return barabasi_albert(n, m_att, gseed)
+
+
 def batch_graphs(count: int, seed: int, n_lo: int = 20, n_hi: int = 2000,
                  p_lo: float = 0.01, p_hi: float = 0.3, m_lo: int = 2, m_hi: int = 6):
-    """`count` graphs: sizes uniform in [n_lo, n_hi]; even index G(n, p) with p
-    uniform in [p_lo, p_hi], odd index Barabasi-Albert with m uniform in [m_lo, m_hi]."""
-    out = []
-    for k in range(count):
-        n = n_lo + stream_draw(seed, 1, k) % (n_hi - n_lo + 1)
-        gseed = stream_draw(seed, 2, k)
-        if k % 2 == 0:
-            u = (stream_draw(seed, 3, k) >> 11) / float(1 << 53)
-            p = p_lo + (p_hi - p_lo) * u
-            out.append(erdos_renyi(n, p, gseed))
-        else:
-            m_att = m_lo + stream_draw(seed, 4, k) % (m_hi - m_lo + 1)
-            out.append(barabasi_albert(n, m_att, gseed))
-    return out
+    """`count` graphs: batch_member(0 .. count-1)."""
+    return [batch_member(k, seed, n_lo, n_hi, p_lo, p_hi, m_lo, m_hi) for k in range(count)]

@@ -168,6 +168,23 @@ int escape_last_phase_ms(const escape_graph* g, float* ms, int count);
 long long escape_last_kernel_launches(const escape_graph* g);
 
 /*
+ * escape_last_basis_counts -- the four counts the paper fits the census's run
+ * time to (Sec. 8, the runtime-prediction figure; Thm 2's bound
+ * O(W + D + DP + DBP + m + n)), from the last escape_census5 call on this
+ * handle:
+ *   out[0] W    wedges, sum_i C(d_i, 2)
+ *   out[1] D    diamonds, sum over edges of C(T_e, 2)
+ *   out[2] DP   directed 3-paths i <- a -> b -> j of the degree-ordered DAG,
+ *               counted as sum over out-edges a -> b of (d+(a) - 1) d+(b)
+ *   out[3] DBP  directed bipyramids: over directed triangles x < y < z,
+ *               C(number of common out-neighbours of x, y, z above z, 2)
+ *   out      host array of 4; written only on success.
+ * EINVAL if the handle has no completed escape_census5 call (escape_census4
+ * does not compute DP and DBP).
+ */
+escape_status escape_last_basis_counts(const escape_graph* g, escape_u128* out);
+
+/*
  * escape_cycles4_noalloc -- per-vertex 4-cycle counts C4(i) and the total C4
  * of a graph, computed without allocating any memory.  (The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
@@ -197,6 +214,48 @@ long long escape_last_kernel_launches(const escape_graph* g);
 #define ESCAPE_NOALLOC_MAX_N 32768
 escape_status escape_cycles4_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t* c4_v,
                                      uint64_t* c4_total, void* stream);
+
+/*
+ * A census split over several processes or GPUs, each holding the whole graph
+ * (the graph is loaded by every part).  Every part runs
+ *   escape_census5_part(g, part, parts, &p, s)
+ * which orients the graph and counts its triangles in full, then counts the
+ * enumeration sweeps (4-cliques, 5-cliques and the per-triangle sums; 4-cycles;
+ * pair, wheel and 5-cycle sweeps; Thms 5-7, 10-14) for the work items it owns
+ * only: vertex ranks r of the degree order (Sec. 3.2) with r mod parts = part.
+ * Its result is
+ *   p.sums       the part's raw 128-bit sums (the first escape_part_sum_count()
+ *                entries; the rest zero); the sums of the phases every part
+ *                repeats are counted by part 0 alone
+ *   per-element  K4 per edge, C4 per edge, C4 per vertex (uint64 arrays of
+ *                nnz, nnz and n entries in the library's internal order, the
+ *                same on every part), read and written with escape_part_counts.
+ * The parts then exchange: every sum added over the parts (exactly, modulo
+ * 2^128), and every per-element array added element-wise over the parts (into
+ * each part's copy with flags | ESCAPE_PART_PUT, or into one part's only).
+ * One part (or each) then calls escape_census5_finish(g, &total, &out, s),
+ * which applies the closed forms to the totals and writes the same census as
+ * escape_census5 (Thm 2, Thm 3, App. B).  This is the one exchange step of the
+ * census: no other data crosses between parts.
+ *   part, parts  0 <= part < parts, else EINVAL
+ *   out/total    host memory
+ * escape_part_counts:
+ *   k4_e, c4_e, c4_v   host (flags without ESCAPE_DEVICE_PTRS) or device
+ *                      arrays of nnz, nnz, n uint64; any may be NULL
+ *   flags              ESCAPE_HOST_PTRS / ESCAPE_DEVICE_PTRS, | ESCAPE_PART_PUT
+ *                      to write the arrays into the handle instead of reading
+ * EINVAL when the handle holds no part (no escape_census5_part since the last
+ * census or finish).  escape_census5_finish releases the part's arrays.
+ */
+#define ESCAPE_PART_SUMS 64
+#define ESCAPE_PART_PUT 4u
+typedef struct { escape_u128 sums[ESCAPE_PART_SUMS]; } escape_part;
+escape_status escape_census5_part(escape_graph* g, int32_t part, int32_t parts, escape_part* out, void* stream);
+escape_status escape_part_counts(escape_graph* g, uint64_t* k4_e, uint64_t* c4_e, uint64_t* c4_v, uint32_t flags,
+                                 void* stream);
+escape_status escape_census5_finish(escape_graph* g, const escape_part* total, escape_census* out, void* stream);
+/* Number of meaningful entries of escape_part.sums. */
+int escape_part_sum_count(void);
 
 void escape_free(escape_graph* g);
 

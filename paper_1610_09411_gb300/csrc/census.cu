@@ -33,6 +33,7 @@
 #include <map>
 #include <mutex>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 namespace esc {
@@ -79,12 +80,13 @@ __global__ void k_vertex_basic(DevGraph g, AccSet acc) {
   int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int ids[8] = {ACC_W, ACC_S3, ACC_S4, ACC_D2D, ACC_DNBR, ACC_N2A, ACC_N3A, ACC_P4A};
-  LocalAcc<8> la;
+  const int ids[9] = {ACC_W, ACC_S3, ACC_S4, ACC_D2D, ACC_DNBR, ACC_N2A, ACC_N3A, ACC_P4A, ACC_DP};
+  LocalAcc<9> la;
   la.zero();
   for (int64_t v = warp; v < g.n; v += nwarps) {
     unsigned long long dv = (unsigned long long)dg_deg(g, v);
-    u128 s1 = 0, s2 = 0, nb = 0, n2a = 0, p4a = 0;
+    unsigned long long dpv = (unsigned long long)dg_outdeg(g, v);
+    u128 s1 = 0, s2 = 0, nb = 0, n2a = 0, p4a = 0, dp = 0;
     for (int64_t p = g.R[v] + lane; p < g.R[v + 1]; p += 32) {
       int32_t a = g.C[p];
       unsigned long long da = (unsigned long long)dg_deg(g, a);
@@ -92,14 +94,19 @@ __global__ void k_vertex_basic(DevGraph g, AccSet acc) {
       s2 += (u128)(da - 1) * (da - 1);
       nb += da;
       n2a += ch2(dv - 1) * (da - 1);
-      if (a > v) p4a += (u128)(dv - 1) * (da - 1);
+      if (a > v) {
+        p4a += (u128)(dv - 1) * (da - 1);
+        dp += (u128)(dpv - 1) * (unsigned long long)dg_outdeg(g, a);   // the path's middle edge v -> a
+      }
     }
     s1 = warp_sum_u128(s1);
     s2 = warp_sum_u128(s2);
     nb = warp_sum_u128(nb);
     n2a = warp_sum_u128(n2a);
     p4a = warp_sum_u128(p4a);
+    dp = warp_sum_u128(dp);
     if (lane == 0) {
+      la.v[8] += dp;
       la.v[0] += ch2(dv);
       la.v[1] += ch3(dv);
       la.v[2] += ch4(dv);
@@ -300,15 +307,26 @@ __global__ void k_vertex_sum_div(DevGraph g, const unsigned long long* E, unsign
 struct CliqueScratch {
   uint64_t* D;         // per CTA: d+ x ceil(d-/64) words
   int64_t d_words;     // capacity per CTA in words
+  uint64_t* G;         // per CTA: the bit matrix and its companions when they exceed shared memory
+  int64_t g_words;     // capacity per CTA in words
 };
+
+// Bytes of the clique pass's work space for out-degree d (B, K4 accumulators,
+// hash of 2 x pow2(2d) ints, T values).
+static inline size_t clique_space(int d) {
+  int w = (d + 63) >> 6, h = 1;
+  while (h < 2 * d) h <<= 1;
+  return sizeof(uint64_t) * ((size_t)d * w + d) + sizeof(int32_t) * (2 * (size_t)h) + sizeof(uint32_t) * d;
+}
 
 // B rows are symmetric (row a = every neighbour of v_a inside N+(x)).
 __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int b, const uint64_t* Da,
                                             const uint64_t* Db, int DW, bool with_k5, unsigned long long& alpha_out,
-                                            unsigned long long& beta_out, unsigned long long& k5_out) {
+                                            unsigned long long& beta_out, unsigned long long& k5_out,
+                                            unsigned long long& above_out) {
   const uint64_t* ra = B + (int64_t)a * W;
   const uint64_t* rb = B + (int64_t)b * W;
-  unsigned long long alpha = 0, k5 = 0;
+  unsigned long long alpha = 0, k5 = 0, above = 0;
   for (int w = 0; w < W; ++w) alpha += __popcll(ra[w] & rb[w]);
   // 5-cliques with lowest vertex x and next two v_a < v_b: every c in the
   // common neighbourhood above b, then every l adjacent to a, b, c above c
@@ -316,6 +334,7 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int
   for (int w = w0; w < W; ++w) {
     uint64_t cm = ra[w] & rb[w];
     if (w == w0) cm &= ~0ull << ((b + 1) & 63);
+    above += __popcll(cm);
     while (cm) {
       int c = w * 64 + __ffsll((long long)cm) - 1;
       cm &= cm - 1;
@@ -333,26 +352,31 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int
   alpha_out = alpha;
   beta_out = beta;
   k5_out = k5;
+  above_out = above;
 }
 
-// Shared-memory layout for the CTA path: hash (2 x hcap ints), nb values,
-// B (d x W u64), K4 accumulators (d u64), T of x's out-edges (d u32).
+// Work-space layout of the CTA path: B (d x W u64), K4 accumulators (d u64),
+// hash (2 x hcap ints), T of x's out-edges (d u32), in shared memory; for
+// out-degrees whose bit matrix does not fit there (GLOBAL_B), the same layout
+// in a per-CTA region of global memory (cs.G, cs.g_words words per CTA).
+// A launch takes the items with dlo < d+ <= dmax and skips the others.
+template <bool GLOBAL_B>
 __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
                                const uint32_t* T, unsigned long long* K4e, AccSet acc, CliqueScratch cs,
-                               int hash_cap, int dmax, unsigned* status, bool with_k5) {
+                               int hash_cap, int dlo, int dmax, unsigned* status, bool with_k5) {
   extern __shared__ uint64_t smem64[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   int W_cap = (dmax + 63) >> 6;
-  uint64_t* B = smem64;                                        // dmax * W_cap
+  uint64_t* B = GLOBAL_B ? cs.G + (int64_t)blockIdx.x * cs.g_words : smem64;   // dmax * W_cap
   unsigned long long* k4x = (unsigned long long*)(B + (int64_t)dmax * W_cap);   // dmax
   int32_t* hk = (int32_t*)(k4x + dmax);                        // hash_cap
   int32_t* hv = hk + hash_cap;                                 // hash_cap
   uint32_t* Tx = (uint32_t*)(hv + hash_cap);                   // dmax
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint64_t* D = cs.D + (int64_t)blockIdx.x * cs.d_words;
-  const int ids[5] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21};
-  LocalAcc<5> la;
+  const int ids[6] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21, ACC_DBP};
+  LocalAcc<6> la;
   la.zero();
   while (true) {
     int64_t it = next_item(qctr, nitems, &sh_item);
@@ -361,10 +385,7 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
     int64_t o = g.op[x], ib = g.R[x];
     int d = (int)(g.R[x + 1] - o);
     int din = (int)(o - ib);
-    if (d > dmax) {     // cannot happen: items are filtered by d+ on the host side
-      if (threadIdx.x == 0) set_err(status, DEVERR_SCRATCH);
-      continue;
-    }
+    if (d <= dlo || d > dmax) continue;        // the other launch's item
     int W = (d + 63) >> 6;
     int DW = (din + 63) >> 6;
     bool use_beta = din > 0 && (int64_t)d * DW <= cs.d_words;
@@ -372,7 +393,7 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
     int hsz = pow2_at_least(2 * d);
     PosHash H{hk, hv, hsz - 1};
     for (int i = threadIdx.x; i < hsz; i += blockDim.x) hk[i] = -1;
-    for (int i = threadIdx.x; i < d * W; i += blockDim.x) B[i] = 0;
+    for (int64_t i = threadIdx.x; i < (int64_t)d * W; i += blockDim.x) B[i] = 0;
     for (int i = threadIdx.x; i < d; i += blockDim.x) { k4x[i] = 0; Tx[i] = T[o + i]; }
     if (use_beta)
       for (int64_t i = threadIdx.x; i < (int64_t)d * DW; i += blockDim.x) D[i] = 0;
@@ -385,8 +406,8 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
       for (int64_t q = g.op[v] + lane; q < g.R[v + 1]; q += 32) {
         int b = H.find(g.C[q]);
         if (b >= 0) {
-          atomicOr((unsigned long long*)&B[a * W + (b >> 6)], 1ull << (b & 63));
-          atomicOr((unsigned long long*)&B[b * W + (a >> 6)], 1ull << (a & 63));
+          atomicOr((unsigned long long*)&B[(int64_t)a * W + (b >> 6)], 1ull << (b & 63));
+          atomicOr((unsigned long long*)&B[(int64_t)b * W + (a >> 6)], 1ull << (a & 63));
         }
       }
     }
@@ -411,9 +432,10 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
         int32_t w = g.C[q];
         int b = H.find(w);
         if (b < 0) continue;
-        unsigned long long alpha, beta, k5;
+        unsigned long long alpha, beta, k5, above;
         clique_edge(B, W, a, b, use_beta ? D + (int64_t)a * DW : nullptr, use_beta ? D + (int64_t)b * DW : nullptr,
-                    DW, with_k5, alpha, beta, k5);
+                    DW, with_k5, alpha, beta, k5, above);
+        la.v[5] += ch2(above);                                    // directed bipyramids on this triangle
         unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
         unsigned long long tab = T[q], txa = Tx[a], txb = Tx[b];
         la.v[0] += alpha;                                         // 3 x K4
@@ -460,8 +482,8 @@ __global__ void __launch_bounds__(CLQ_WARPS * 32, 4) k_clique_warp(DevGraph g, c
   int32_t* L = sL[wl];
   unsigned long long* Bw = sB[wl];
   unsigned long long* K = sK[wl];
-  const int ids[5] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21};
-  LocalAcc<5> la;
+  const int ids[6] = {ACC_K4, ACC_N20, ACC_N10A, ACC_N16A, ACC_N21, ACC_DBP};
+  LocalAcc<6> la;
   la.zero();
   // position of vertex key in N+(x) (sorted, padded with INT32_MAX), or -1
   auto find = [&](int32_t key) -> int {
@@ -538,6 +560,7 @@ __global__ void __launch_bounds__(CLQ_WARPS * 32, 4) k_clique_warp(DevGraph g, c
         // 5-cliques at the three lowest vertices x, v_a, v_b: every c in the
         // common neighbourhood above b, then every l adjacent to a, b, c above c
         unsigned long long cm2 = with_k5 ? cm & (~0ull << (b + 1)) : 0ull;
+        la.v[5] += ch2((unsigned long long)__popcll(cm2));        // directed bipyramids on this triangle
         while (cm2) {
           int c = __ffsll((long long)cm2) - 1;
           cm2 &= cm2 - 1;
@@ -587,9 +610,11 @@ struct TaggedCounters {
   unsigned long long* wb;
   int32_t jbig;
   uint32_t tag;
-  __device__ TaggedCounters(const TagScratch& ts) {
-    w = ts.w + (int64_t)blockIdx.x * ts.jbig;
-    wb = ts.wb + (int64_t)blockIdx.x * (ts.n - ts.jbig);
+  __device__ TaggedCounters(const TagScratch& ts) : TaggedCounters(ts, blockIdx.x) {}
+  // the array of index `arr` (one per CTA, or one per cluster of CTAs)
+  __device__ TaggedCounters(const TagScratch& ts, int64_t arr) {
+    w = ts.w + arr * ts.jbig;
+    wb = ts.wb + arr * (ts.n - ts.jbig);
     jbig = (int32_t)ts.jbig;
     tag = 0;
   }
@@ -620,18 +645,64 @@ struct TaggedCounters {
     unsigned long long v = wb[j - jbig];
     return (uint32_t)(v >> 32) == tag ? (uint32_t)v : 0u;
   }
+  // get() for an array that CTAs of other SMs increment: read at L2 (the
+  // increments are performed there; an L1 copy could be stale)
+  __device__ __forceinline__ uint32_t get_l2(int32_t j) const {
+    if (!BIG || j < jbig) {
+      uint32_t v = __ldcg(&w[j]);
+      return (v >> 16) == tag ? (v & 0xffffu) : 0u;
+    }
+    unsigned long long v = __ldcg(&wb[j - jbig]);
+    return (uint32_t)(v >> 32) == tag ? (uint32_t)v : 0u;
+  }
   // next item: a new tag, or zeroed counters once the tags are used up (all
   // threads of the CTA call it; returns true when it zeroed, and a barrier
   // must then publish the zeros before the next increment)
-  __device__ __forceinline__ bool next(int64_t n) {
+  __device__ __forceinline__ bool next(int64_t n) { return next_shared(n, 0, 1); }
+  // the same for an array shared by the `parts` CTAs of a cluster: CTA
+  // `part` zeroes its share, and a cluster barrier must follow a zeroing
+  __device__ __forceinline__ bool next_shared(int64_t n, unsigned part, unsigned parts) {
     if (++tag <= TAG_MAX) return false;
-    for (int64_t t = threadIdx.x; t < jbig; t += blockDim.x) w[t] = 0;
+    const int64_t t0 = (int64_t)part * blockDim.x + threadIdx.x, st = (int64_t)parts * blockDim.x;
+    for (int64_t t = t0; t < jbig; t += st) w[t] = 0;
     if (BIG)
-      for (int64_t t = threadIdx.x; t < n - jbig; t += blockDim.x) wb[t] = 0;
+      for (int64_t t = t0; t < n - jbig; t += st) wb[t] = 0;
     tag = 1;
     return true;
   }
 };
+
+// ---------------------------------------------------------------- clusters
+// Thread-block cluster helpers (PTX special registers and the hardware
+// cluster barrier).  A kernel launched without a cluster dimension runs as
+// clusters of one CTA, for which these reduce to the CTA itself.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; orders memory at cluster scope
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// 64-bit value at the address of `p` in the shared memory of cluster CTA `rank`
+__device__ __forceinline__ long long ld_cluster_s64(const void* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  long long v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
+  return v;
+}
 
 // ============================================================================
 // Thm 5: 4-cycles.  For the highest vertex i and each j < i,
@@ -644,13 +715,11 @@ struct TaggedCounters {
 #define ESC_SWEEP_ILP 8
 #endif
 static constexpr int SWEEP_ILP = ESC_SWEEP_ILP;   // independent accesses in flight per lane (4- and 5-cycles)
-// The pair sweep runs three 512-thread CTAs per SM (40 registers a thread),
-// which leaves room for fewer accesses in flight per lane.
+// The pair sweep keeps fewer accesses in flight per lane (its CTAs are larger).
 #ifndef ESC_PAIR_ILP
 #define ESC_PAIR_ILP 4
 #endif
 static constexpr int PAIR_ILP = ESC_PAIR_ILP;
-static constexpr int PAIR_CTAS_PER_SM = 3;
 
 struct SweepScratch {
   uint32_t* cnt;       // per CTA: n counters (kept zero between items)
@@ -663,16 +732,16 @@ struct SweepScratch {
 
 template <bool BIG>
 __global__ void k_cycles4(DevGraph g, unsigned long long* qctr, TagScratch ts, unsigned long long* C4raw,
-                          unsigned long long* C4v, AccSet acc) {
+                          unsigned long long* C4v, AccSet acc, Owner own) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   TaggedCounters<BIG> w(ts);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   u128 c4sum = 0;
   while (true) {
-    int64_t it = next_item(qctr, g.n, &sh_item);
+    int64_t it = next_item(qctr, own.count(g.n), &sh_item);
     if (it < 0) break;
-    int64_t i = g.n - 1 - it;
+    int64_t i = own.item(g.n, it);
     int64_t b0 = g.R[i], e0 = g.op[i];
     if (e0 == b0) continue;           // no lower neighbours
     if (w.next(g.n)) __syncthreads();
@@ -772,98 +841,350 @@ struct TriLists {
 // ============================================================================
 
 
-template <bool BIG>
-__global__ void __launch_bounds__(512, PAIR_CTAS_PER_SM) k_pairs(DevGraph g, unsigned long long* qctr, int64_t item_lo,
-                                                  int64_t item_hi, TagScratch ts, TriLists tl3, const uint32_t* T,
-                                                  AccSet acc) {
+// Items are split by their wedge count w_i = sum_{c in N(i)} |N(c) below i|
+// (the number of W(i, .) increments, so also a bound on the distinct j):
+//   light  (w_i <= PH_SMALL_W): one CTA, W(i, .) in a shared-memory hash table
+//   medium (w_i <= PH_LARGE_W): one CTA, a larger shared-memory hash table
+//   heavy:                      a cluster of CTAs shares one tagged counter
+//                               array in global memory, and only as many
+//                               clusters run as keep their arrays within L2
+static constexpr int PH_SMALL_SLOTS = 4096, PH_SMALL_THREADS = 256;
+static constexpr int PH_LARGE_SLOTS = 16384, PH_LARGE_THREADS = 512;
+static constexpr int64_t PH_SMALL_W = PH_SMALL_SLOTS / 2;     // load factor <= 1/2
+static constexpr int64_t PH_LARGE_W = PH_LARGE_SLOTS / 2;
+
+// w_i of every vertex with degree >= 2, appended to the list of its class
+// (roughly by decreasing rank, so the heaviest items come first)
+__global__ void k_pair_classify(DevGraph g, int32_t* lists, unsigned long long* cnts, long long w_small,
+                                long long w_large, Owner own) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = warp; k < g.n; k += nwarps) {
+    int64_t i = g.n - 1 - k;
+    int64_t b0 = g.R[i], e0 = g.R[i + 1];
+    if (e0 - b0 < 2 || !own.owns(i)) continue;
+    unsigned long long w = 0;
+    for (int64_t p = b0 + lane; p < e0; p += 32) w += (unsigned long long)(g.rev[p] - g.R[g.C[p]]);
+    w = warp_sum_u64(w);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w == 0) continue;
+    int cls = (long long)w <= w_small ? 0 : ((long long)w <= w_large ? 1 : 2);
+    if (lane == 0) {
+      lists[(int64_t)cls * g.n + (int64_t)atomicAdd(&cnts[cls], 1ull)] = (int32_t)i;
+      if (cls == 2) atomicMax(&cnts[6], w);    // the largest item, for the task buffers
+    }
+  }
+}
+
+// Open addressing in shared memory (keys -1 = empty), linear probing.  At most
+// half the slots are ever used, so a probe sequence ends within the table.
+template <int SLOTS>
+__device__ __forceinline__ int ph_insert(int32_t* hk, int32_t j) {
+  constexpr int LOG = __builtin_ctz(SLOTS);
+  uint32_t sl = ((uint32_t)j * 0x9E3779B1u) >> (32 - LOG);
+  volatile int32_t* vk = hk;
+  for (int probe = 0; probe < SLOTS; ++probe) {
+    int32_t k = vk[sl];
+    if (k == j) return (int)sl;
+    if (k == -1) {
+      int32_t old = atomicCAS(&hk[sl], -1, j);
+      if (old == -1 || old == j) return (int)sl;
+    }
+    sl = (sl + 1) & (SLOTS - 1);
+  }
+  return -1;
+}
+template <int SLOTS>
+__device__ __forceinline__ int ph_find(const int32_t* hk, int32_t j) {
+  constexpr int LOG = __builtin_ctz(SLOTS);
+  uint32_t sl = ((uint32_t)j * 0x9E3779B1u) >> (32 - LOG);
+  for (int probe = 0; probe < SLOTS; ++probe) {
+    int32_t k = hk[sl];
+    if (k == j) return (int)sl;
+    if (k == -1) return -1;
+    sl = (sl + 1) & (SLOTS - 1);
+  }
+  return -1;
+}
+
+// The two passes of one item i, shared by both forms of the sweep.  Warp
+// `gw` of `gnw` (the warps of a CTA, or of a whole cluster) takes its share:
+//   inc(j) counts the wedge i - c - j and returns W(i,j) before it;
+//   get(j) returns W(i,j) after every increment.
+// Pass 1: W(i,.) from every wedge i - c - j (c in N(i), j in N(c), j < i);
+// C(W,3) is accumulated on the fly as the sum of C(old, 2).  The lists N(c) are
+// fetched 32 per warp (lane k the k-th) and every lane keeps PAIR_ILP
+// independent loads and counter operations in flight.
+static constexpr int PAIR_TASK = 32 * 4 * 4;   // lists longer than this are shared as tasks of this size
+
+// Increments for the entries C[cb .. ce) (one warp, PAIR_ILP loads per lane in flight).
+template <class Inc>
+__device__ __forceinline__ u128 pair_range(const DevGraph& g, int64_t cb, int64_t ce, Inc&& inc) {
+  const int lane = threadIdx.x & 31;
+  u128 n13 = 0;
+  for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
+    int32_t jj[PAIR_ILP];
+    uint32_t oo[PAIR_ILP];
+#pragma unroll
+    for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? __ldcs(&g.C[q + 32 * u]) : -1;
+#pragma unroll
+    for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? inc(jj[u]) : 1u;
+#pragma unroll
+    for (int u = 0; u < PAIR_ILP; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;   // zero for old = 0 and 1
+  }
+  return n13;
+}
+
+// defer(cb, ce) may take a long list off the warp (returning true) so that
+// every warp shares it later; it is called by all 32 lanes with the same range.
+template <class Inc, class Defer>
+__device__ __forceinline__ u128 pair_wedges(const DevGraph& g, int64_t b0, int64_t e0, int64_t gw, int64_t gnw,
+                                            Inc&& inc, Defer&& defer) {
+  const int lane = threadIdx.x & 31;
+  u128 n13 = 0;
+  for (int64_t pbase = b0 + gw; pbase < e0; pbase += gnw * 32) {
+    int64_t p = pbase + (int64_t)lane * gnw;
+    int64_t cb_l = 0, ce_l = 0;
+    if (p < e0) {
+      int32_t c = g.C[p];
+      cb_l = g.R[c];
+      ce_l = g.rev[p];                          // N(c) below i ends at the slot of i
+    }
+    int kmax = (int)min((int64_t)32, (e0 - pbase + gnw - 1) / gnw);
+    for (int k = 0; k < kmax; ++k) {
+      int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
+      if (ce - cb > PAIR_TASK && defer(cb, ce)) continue;
+      n13 += pair_range(g, cb, ce, inc);
+    }
+  }
+  return n13;
+}
+
+// Long lists split into tasks of PAIR_TASK entries, shared by all warps of a
+// CTA or cluster: per work group a task array (entry ranges of C) and a count.
+struct PairTasks {
+  long long* q;             // per group: cap x (begin, end)
+  unsigned long long* n;    // per group: number of tasks (zero between items)
+  int64_t cap;              // tasks per group
+};
+
+// Appends the tasks of list [cb, ce) to group `grp`; false if they do not fit
+// (the caller then counts the list itself).  All 32 lanes call it.
+__device__ __forceinline__ bool pair_defer(const PairTasks& pt, int64_t grp, int64_t cb, int64_t ce) {
+  const int lane = threadIdx.x & 31;
+  const long long nt = (ce - cb + PAIR_TASK - 1) / PAIR_TASK;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&pt.n[grp], (unsigned long long)nt);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if ((long long)base + nt > pt.cap) return false;   // never: sized by the largest item
+  long long* q = pt.q + 2 * (grp * pt.cap + (long long)base);
+  for (long long t = lane; t < nt; t += 32) {
+    long long a = cb + t * PAIR_TASK;
+    q[2 * t] = a;
+    q[2 * t + 1] = min((long long)ce, a + PAIR_TASK);
+  }
+  return true;
+}
+
+// The tasks of group `grp`, task t taken by warp t mod gnw.
+// nt: the group's task count, read after the barrier that ends the appends
+template <class Inc>
+__device__ __forceinline__ u128 pair_run_tasks(const DevGraph& g, const PairTasks& pt, int64_t grp,
+                                               unsigned long long nt, int64_t gw, int64_t gnw, Inc&& inc) {
+  nt = min(nt, (unsigned long long)pt.cap);
+  const long long* q = pt.q + 2 * grp * pt.cap;
+  u128 n13 = 0;
+  for (unsigned long long t = (unsigned long long)gw; t < nt; t += (unsigned long long)gnw)
+    n13 += pair_range(g, __ldcg(&q[2 * t]), __ldcg(&q[2 * t + 1]), inc);
+  return n13;
+}
+
+// Pass 2: the cc term per diamond with tip i.  For each x in N(i), the
+// triangles {i, x, y} with y above x are a suffix of the position list of
+// slot (x -> i); the common-neighbour list of (x, y) is sorted, so the j
+// below i are a prefix of it; each adds W(i,j) - 2 (Thm 12's enumeration
+// through the per-edge triangle lists).
+// The diamonds of one chunk of at most 32 triangles {i, x, y}: positions
+// [r0, r1) of the position list of slot (x -> i), x = C[p] (lane k takes the
+// k-th y; the whole warp then walks each y's common-neighbour list).
+template <class Get>
+__device__ __forceinline__ u128 pair_diamond_chunk(const DevGraph& g, const TriLists& tl3, const uint32_t* T,
+                                                   int64_t i, int64_t xb, int64_t r0, int64_t r1, Get&& get) {
+  const int lane = threadIdx.x & 31;
+  u128 n17 = 0;
+  int64_t r = r0 + lane;
+  int64_t vb_l = 0;
+  uint32_t len_l = 0;
+  if (r < r1) {
+    int64_t sxy = xb + tl3.P[r];                // slot (x -> y)
+    vb_l = tl3.off[sxy];
+    len_l = T[sxy];
+  }
+  int kmax = (int)min((int64_t)32, r1 - r0);
+  for (int k = 0; k < kmax; ++k) {
+    int64_t vb = __shfl_sync(0xffffffffu, vb_l, k);
+    int64_t ve = vb + __shfl_sync(0xffffffffu, len_l, k);
+    for (int64_t sb = vb; sb < ve; sb += 32 * PAIR_ILP) {
+      int32_t jj[PAIR_ILP];
+      bool past = false;
+#pragma unroll
+      for (int u = 0; u < PAIR_ILP; ++u) {
+        int64_t s_ = sb + lane + 32 * u;
+        jj[u] = s_ < ve ? __ldcs(&tl3.U[s_]) : 0x7fffffff;
+        if (jj[u] >= i) { jj[u] = -1; past = true; }
+      }
+#pragma unroll
+      for (int u = 0; u < PAIR_ILP; ++u)
+        if (jj[u] >= 0) n17 += (u128)(get(jj[u]) - 2);   // x, y are common neighbours of i, j
+      if (__any_sync(0xffffffffu, past)) break;
+    }
+  }
+  return n17;
+}
+
+// The triangles {i, x, y} with y above x of slot p = (i -> x): positions
+// [r0, r1) of the position list of slot (x -> i); r0 = r1 if there are none.
+__device__ __forceinline__ void pair_tri_range(const DevGraph& g, const TriLists& tl3, const uint32_t* T, int64_t p,
+                                               int64_t& xb, int64_t& r0, int64_t& r1) {
+  int32_t x = g.C[p];
+  xb = g.R[x];
+  int32_t xo = (int32_t)(g.op[x] - xb);         // positions >= xo in row x are above x
+  int64_t rp_ = g.rev[p];                       // slot (x -> i)
+  int64_t yb = tl3.offp[rp_];
+  r1 = yb + T[rp_];
+  r0 = lower_bound_i32(tl3.P, yb, r1, xo);
+}
+
+template <class Get>
+__device__ __forceinline__ u128 pair_diamonds(const DevGraph& g, const TriLists& tl3, const uint32_t* T, int64_t i,
+                                              int64_t b0, int64_t e0, int64_t gw, int64_t gnw, Get&& get) {
+  u128 n17 = 0;
+  for (int64_t p = b0 + gw; p < e0; p += gnw) {
+    if (T[p] == 0) continue;
+    int64_t xb, r0, r1;
+    pair_tri_range(g, tl3, T, p, xb, r0, r1);
+    for (int64_t rb = r0; rb < r1; rb += 32) n17 += pair_diamond_chunk(g, tl3, T, i, xb, rb, min(rb + 32, r1), get);
+  }
+  return n17;
+}
+
+// Light and medium items: one CTA per item, W(i, .) in a shared-memory hash
+// table (SLOTS keys and counts) that is cleared after every item.
+template <int SLOTS>
+__global__ void k_pairs_hash(DevGraph g, const int32_t* items, int64_t nitems, unsigned long long* qctr,
+                             TriLists tl3, const uint32_t* T, AccSet acc, unsigned* status) {
+  extern __shared__ int32_t ph_smem[];
+  int32_t* hk = ph_smem;
+  uint32_t* hv = (uint32_t*)(ph_smem + SLOTS);
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  TaggedCounters<BIG> w(ts);
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ids[2] = {ACC_N13, ACC_N17};
   LocalAcc<2> la;
   la.zero();
+  for (int t = threadIdx.x; t < SLOTS; t += blockDim.x) { hk[t] = -1; hv[t] = 0u; }
   while (true) {
-    int64_t it = next_item(qctr, item_hi - item_lo, &sh_item);
+    int64_t it = next_item(qctr, nitems, &sh_item);     // its barriers publish the cleared table
     if (it < 0) break;
-    int64_t i = g.n - 1 - (item_lo + it);
-    int64_t b0 = g.R[i], e0 = g.R[i + 1];
-    if (e0 - b0 < 2) continue;
-    if (w.next(ts.n)) __syncthreads();
-    u128 n13 = 0, n17 = 0;
-    // The warp's lists are fetched 32 at a time (lane k holds the k-th), and
-    // each lane keeps PAIR_ILP independent loads and counter operations in
-    // flight: the sweep is bound by the latency of scattered accesses.
-    for (int64_t pbase = b0 + wid; pbase < e0; pbase += (int64_t)nw * 32) {
-      int64_t p = pbase + (int64_t)lane * nw;
-      int64_t cb_l = 0, ce_l = 0;
-      if (p < e0) {
-        int32_t c = g.C[p];
-        cb_l = g.R[c];
-        ce_l = g.rev[p];                        // N(c) below i ends at the slot of i
-      }
-      int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
-      for (int k = 0; k < kmax; ++k) {
-        int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
-        for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
-          int32_t jj[PAIR_ILP];
-          uint32_t oo[PAIR_ILP];
-#pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : -1;
-#pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? w.inc(jj[u]) : 1u;
-#pragma unroll
-          for (int u = 0; u < PAIR_ILP; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;   // zero for old = 0 and 1
-        }
-      }
-    }
+    const int64_t i = items[it];
+    const int64_t b0 = g.R[i], e0 = g.R[i + 1];
+    u128 n13 = pair_wedges(g, b0, e0, wid, nw, [&](int32_t j) -> uint32_t {
+      int sl = ph_insert<SLOTS>(hk, j);
+      if (sl < 0) { set_err(status, DEVERR_SCRATCH); return 0u; }
+      return atomicAdd(&hv[sl], 1u);
+    }, [](int64_t, int64_t) { return false; });
     __syncthreads();
-    // diamonds with tip i: for each x in N(i) the triangles {i, x, y} with y
-    // above x (a suffix of the position list of slot (x -> i)); their
-    // common-neighbour lists are sorted, so the j below i are a prefix
-    for (int64_t p = b0 + wid; p < e0; p += nw) {
-      if (T[p] == 0) continue;
-      int32_t x = g.C[p];
-      int64_t xb = g.R[x];
-      int32_t xo = (int32_t)(g.op[x] - xb);     // positions >= xo in row x are above x
-      int64_t rp_ = g.rev[p];                   // slot (x -> i)
-      int64_t yb = tl3.offp[rp_];
-      int64_t ye = yb + T[rp_];
-      for (int64_t rb = lower_bound_i32(tl3.P, yb, ye, xo); rb < ye; rb += 32) {
-        int64_t r = rb + lane;
-        int64_t vb_l = 0;
-        uint32_t len_l = 0;
-        if (r < ye) {
-          int64_t sxy = xb + tl3.P[r];          // slot (x -> y)
-          vb_l = tl3.off[sxy];
-          len_l = T[sxy];
-        }
-        int kmax = (int)min((int64_t)32, ye - rb);
-        for (int k = 0; k < kmax; ++k) {
-          int64_t vb = __shfl_sync(0xffffffffu, vb_l, k);
-          int64_t ve = vb + __shfl_sync(0xffffffffu, len_l, k);
-          for (int64_t sb = vb; sb < ve; sb += 32 * PAIR_ILP) {
-            int32_t jj[PAIR_ILP];
-            bool past = false;
-#pragma unroll
-            for (int u = 0; u < PAIR_ILP; ++u) {
-              int64_t s_ = sb + lane + 32 * u;
-              jj[u] = s_ < ve ? tl3.U[s_] : 0x7fffffff;
-              if (jj[u] >= i) { jj[u] = -1; past = true; }
-            }
-#pragma unroll
-            for (int u = 0; u < PAIR_ILP; ++u)
-              if (jj[u] >= 0) n17 += (u128)(w.get(jj[u]) - 2);   // x, y are common neighbours of i, j
-            if (__any_sync(0xffffffffu, past)) break;
-          }
-        }
-      }
-    }
+    u128 n17 = pair_diamonds(g, tl3, T, i, b0, e0, wid, nw, [&](int32_t j) -> uint32_t {
+      int sl = ph_find<SLOTS>(hk, j);
+      if (sl < 0) { set_err(status, DEVERR_SCRATCH); return 2u; }
+      return hv[sl];
+    });
+    __syncthreads();
+    for (int t = threadIdx.x; t < SLOTS; t += blockDim.x) { hk[t] = -1; hv[t] = 0u; }
     la.v[0] += n13;
     la.v[1] += n17;
     block_item_flush(la, ids, acc, i, sh);
-    __syncthreads();
   }
+  final_flush(la, ids, acc, sh);
+}
+
+// Heavy items: all CTAs of a cluster work on one item at a time, with one
+// tagged counter array per cluster (index %clusterid.x).  CTA 0 of the
+// cluster takes the next item from the queue and the others read it from its
+// shared memory; two cluster barriers per item order the increments before
+// the reads and the reads before the next item's increments.
+// Lists longer than PAIR_TASK entries are cut into tasks that every warp of
+// the cluster shares after a barrier, so one hub's list does not hold the
+// cluster back.
+//
+// With clusters of one CTA, the counters of the ranks [wlo, jbig) -- the top
+// ranks below the 64-bit side array, where nearly all the diamond reads and a
+// good share of the increments land (measured: the top 16K ranks take 94% of
+// the diamond reads on the Chung-Lu workload, the top 64K 98% on R-MAT scale
+// 20) -- live in shared memory as 16-bit counts, two to a word, cleared for
+// every item (a count there is at most the rank's degree, below 2^16).
+template <bool BIG, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_pairs_grp(DevGraph g, const int32_t* items,
+                                                                         int64_t nitems, unsigned long long* qctr,
+                                                                         TagScratch ts, TriLists tl3,
+                                                                         const uint32_t* T, AccSet acc,
+                                                                         PairTasks pt, int64_t wlo, int win_words) {
+  extern __shared__ uint32_t win[];
+  __shared__ u128 sh[32];
+  __shared__ long long sh_item;
+  const unsigned crank = cluster_rank(), csize = cluster_size();
+  const int64_t grp = (int64_t)cluster_index();
+  TaggedCounters<BIG> w(ts, grp);
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t gw = (int64_t)crank * nw + wid, gnw = (int64_t)csize * nw;
+  const int ids[2] = {ACC_N13, ACC_N17};
+  const int64_t whi = win_words > 0 ? min(ts.jbig, wlo + 2 * (int64_t)win_words) : wlo;   // window [wlo, whi)
+  LocalAcc<2> la;
+  la.zero();
+  while (true) {
+    if (crank == 0 && threadIdx.x == 0) {
+      sh_item = (long long)atomicAdd(qctr, 1ull);
+      pt.n[grp] = 0;                           // every CTA is past the last item's tasks
+    }
+    cluster_barrier();                         // also: the last item's reads are done
+    const long long it = ld_cluster_s64(&sh_item, 0);
+    if (it >= nitems) break;
+    const int64_t i = items[it];
+    const int64_t b0 = g.R[i], e0 = g.R[i + 1];
+    if (w.next_shared(ts.n, crank, csize)) cluster_barrier();
+    if (win_words > 0) {
+      for (int t = threadIdx.x; t < win_words; t += blockDim.x) win[t] = 0u;
+      cluster_barrier();
+    }
+    auto inc = [&](int32_t j) -> uint32_t {
+      if (j >= wlo && j < whi) {
+        const int64_t k = j - wlo;
+        const unsigned sh16 = 16u * (unsigned)(k & 1);
+        return (atomicAdd(&win[k >> 1], 1u << sh16) >> sh16) & 0xffffu;
+      }
+      return w.inc(j);
+    };
+    u128 n13 = pair_wedges(g, b0, e0, gw, gnw, inc,
+                           [&](int64_t cb, int64_t ce) { return pair_defer(pt, grp, cb, ce); });
+    cluster_barrier();
+    // the task count is read before the next barrier, after which CTA 0 may
+    // clear it for the next item
+    const unsigned long long nt1 = __ldcg(&pt.n[grp]);
+    n13 += pair_run_tasks(g, pt, grp, nt1, gw, gnw, inc);
+    cluster_barrier();
+    u128 n17 = pair_diamonds(g, tl3, T, i, b0, e0, gw, gnw, [&](int32_t j) -> uint32_t {
+      if (j >= wlo && j < whi) {
+        const int64_t k = j - wlo;
+        return (win[k >> 1] >> (16u * (unsigned)(k & 1))) & 0xffffu;
+      }
+      return w.get_l2(j);
+    });
+    la.v[0] += n13;
+    la.v[1] += n17;
+    block_item_flush(la, ids, acc, i, sh);
+  }
+  cluster_barrier();                           // CTA 0's shared memory stays until every CTA has read it
   final_flush(la, ids, acc, sh);
 }
 
@@ -941,11 +1262,11 @@ __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t*
 static constexpr int WHEEL_WBLK = 32;
 
 // item_cnt[k] = number of items of centre c0 - 1 - k (position k in the queue)
-__global__ void k_wheel_warp_counts(DevGraph g, int64_t c0, int64_t* item_cnt) {
+__global__ void k_wheel_warp_counts(DevGraph g, int64_t c0, int64_t* item_cnt, Owner own) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < c0; k += (int64_t)gridDim.x * blockDim.x) {
     int64_t c = c0 - 1 - k;
     int64_t d = g.R[c + 1] - g.R[c];
-    item_cnt[k] = d >= 4 ? (d + WHEEL_WBLK - 1) / WHEEL_WBLK : 0;
+    item_cnt[k] = d >= 4 && own.owns(c) ? (d + WHEEL_WBLK - 1) / WHEEL_WBLK : 0;
   }
 }
 
@@ -1084,7 +1405,7 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
 // ============================================================================
 template <bool BIG>
 __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long long* qctr, TagScratch ts,
-                                                   SweepScratch ss, AccSet acc) {
+                                                   SweepScratch ss, AccSet acc, Owner own) {
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
   TaggedCounters<BIG> wp(ts);                                                         // w'(i, .)
@@ -1096,9 +1417,9 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
   LocalAcc<1> la;
   la.zero();
   while (true) {
-    int64_t it = next_item(qctr, g.n, &sh_item);
+    int64_t it = next_item(qctr, own.count(g.n), &sh_item);
     if (it < 0) break;
-    int64_t i = g.n - 1 - it;
+    int64_t i = own.item(g.n, it);
     int64_t b0 = g.R[i], o = g.op[i], e0 = g.R[i + 1];
     if (o == b0) continue;                      // needs an in-neighbour a
     wp.next(ts.n);
@@ -1340,14 +1661,23 @@ __device__ __forceinline__ u128 cnk(u128 n, int k) {
 }
 
 // One thread per graph: graph k reads accumulator row k and writes result k.
+// basis_all (optional): per graph the four counts the runtime is linear in
+// (Sec. 8's runtime fit): W, D, directed 3-paths, directed bipyramids.
 __global__ void k_assemble(const Acc128* acc_all, const unsigned long long* n_arr, const unsigned long long* m_arr,
-                           int num_graphs, ConvTables tabs, unsigned long long* out_all) {
+                           int num_graphs, ConvTables tabs, unsigned long long* out_all, u128* basis_all) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= num_graphs) return;
   const Acc128* acc = acc_all + (int64_t)k * ACC_COUNT;
   unsigned long long* out = out_all + (int64_t)k * 2 * 98;
   u128 A[ACC_COUNT];
   for (int i = 0; i < ACC_COUNT; ++i) A[i] = ((u128)acc[i].hi << 64) | acc[i].lo;
+  if (basis_all) {
+    u128* bo = basis_all + (int64_t)k * 4;
+    bo[0] = A[ACC_W];
+    bo[1] = A[ACC_D];
+    bo[2] = A[ACC_DP];
+    bo[3] = A[ACC_DBP];
+  }
   u128 n = n_arr[k], m = m_arr[k];
   u128 W = A[ACC_W], T = A[ACC_T], TT = A[ACC_TT], C4 = A[ACC_C4], D = A[ACC_D];
   u128 K4 = A[ACC_K4] / 3, S3 = A[ACC_S3];
@@ -1444,19 +1774,24 @@ __global__ void k_graph_sizes(const int64_t* voff, const int64_t* rp, int num_gr
 // small / large: d+ up to small_max or above (vertices with d+ >= 2); the
 // small ones are also split by d- for the clique pass: up to warp_din in wsmall
 // (one warp each), the rest in csmall (one CTA each).
+// The clique pass takes only the owned vertices (wsmall, csmall, clarge);
+// the triangle pass takes every vertex (small, large).
 __global__ void k_split_items(DevGraph g, int32_t* small, int32_t* large, int32_t* wsmall, int32_t* csmall,
-                              unsigned long long* cnts, int small_max, int warp_din) {
+                              int32_t* clarge, unsigned long long* cnts, int small_max, int warp_din, Owner own) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < g.n; k += stride) {
     int64_t x = g.n - 1 - k;
     int64_t d = g.R[x + 1] - g.op[x];
     if (d < 2) continue;
+    const bool mine = own.owns(x);
     if (d <= small_max) {
       small[atomicAdd(&cnts[0], 1ull)] = (int32_t)x;
+      if (!mine) continue;
       if (g.op[x] - g.R[x] <= warp_din) wsmall[atomicAdd(&cnts[2], 1ull)] = (int32_t)x;
       else csmall[atomicAdd(&cnts[3], 1ull)] = (int32_t)x;
     } else {
       large[atomicAdd(&cnts[1], 1ull)] = (int32_t)x;
+      if (mine) clarge[atomicAdd(&cnts[4], 1ull)] = (int32_t)x;
     }
   }
 }
@@ -1648,6 +1983,131 @@ static cudaError_t allow_max_smem(const void* k, int optin) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
+// Launch shape of the heavy pair items: CTAs of `threads` threads grouped in
+// clusters of `cs`, `nclusters` clusters (one counter array each), as many
+// clusters as the SMs hold.  ESC_PAIR_SHAPE, ESC_PAIR_CLUSTER and
+// ESC_PAIR_CLUSTERS override the choice (tuning only; results are the same).
+struct PairPlan {
+  int cs = 1, threads = 512, nclusters = 0;
+  int shape = 1;                               // kernel instance, see ESC_PAIR_SHAPES
+  int win_words = 0;                           // shared-memory window (clusters of one CTA)
+  int64_t wlo = 0;                             // its first rank
+};
+
+static int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  if (!v || !*v) return dflt;
+  int x = atoi(v);
+  return x > 0 ? x : dflt;
+}
+
+// Launch shapes of the heavy-item kernel: (threads, CTAs per SM) = (512, 3)
+// at 40 registers, (512, 2) at 64, (1024, 1) at 64.
+#define ESC_PAIR_SHAPES(X) X(0, 512, 3) X(1, 512, 2) X(2, 1024, 1)
+static const void* pairs_grp_fn(bool big, int shape) {
+#define ESC_PG(k, t, b) if (shape == k) return big ? (const void*)k_pairs_grp<true, t, b> : (const void*)k_pairs_grp<false, t, b>;
+  ESC_PAIR_SHAPES(ESC_PG)
+#undef ESC_PG
+  return nullptr;
+}
+
+static cudaError_t plan_pair_clusters(bool big, int sms, size_t arr_bytes, int64_t n0, int64_t jbig, int smem_optin,
+                                      PairPlan* plan) {
+  // default: the window with one 1024-thread CTA per SM (its window is twice
+  // as wide as two 512-thread CTAs' each); without the window, (512, 2)
+  const bool window = env_int("ESC_PAIR_CLUSTER", 1) == 1 && env_int("ESC_PAIR_WINDOW", 2) != 1;
+  plan->shape = std::min(2, env_int("ESC_PAIR_SHAPE", window ? 3 : 2) - 1);
+  plan->threads = plan->shape == 2 ? 1024 : 512;
+  const void* k = pairs_grp_fn(big, plan->shape);
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  ESC_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  const size_t budget = (size_t)std::max(l2, 1 << 20) / 2;
+  const int64_t kmax = std::max<int64_t>(1, (int64_t)(budget / std::max<size_t>(arr_bytes, 1)));
+  // the window: what shared memory leaves per CTA, for clusters of one CTA
+  // (ESC_PAIR_WINDOW=1 turns it off)
+  plan->win_words = 0;
+  plan->wlo = jbig;
+  if (window) {
+    cudaFuncAttributes fa;
+    ESC_TRY(cudaFuncGetAttributes(&fa, k));
+    const int per_sm_target = plan->threads == 1024 ? 1 : 2;
+    int bytes = (smem_optin / per_sm_target - (int)fa.sharedSizeBytes - 1024) & ~15;
+    int64_t want = std::max<int64_t>(0, (jbig - n0 + 1) / 2);        // words covering every countable rank
+    plan->win_words = (int)std::max<int64_t>(0, std::min<int64_t>(bytes / 4, want));
+    plan->wlo = std::max<int64_t>(n0, jbig - 2 * (int64_t)plan->win_words);
+    if (plan->win_words > 0)
+      ESC_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->win_words * 4));
+  }
+  int per_sm = 1;
+  ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan->threads, plan->win_words * 4));
+  const int64_t total = (int64_t)sms * std::max(1, per_sm);
+  // clusters of one CTA with the shared-memory window by default; without
+  // it, clusters of 4 CTAs were fastest on the Chung-Lu and R-MAT workloads,
+  // ahead of the larger clusters whose fewer arrays stay in L2 (the items in
+  // flight matter more than L2 hits); kmax, the cluster count that would fit
+  // L2, is kept for the record of the plan
+  int cs = env_int("ESC_PAIR_CLUSTER", plan->win_words > 0 ? 1 : 4);
+  (void)kmax;
+  plan->nclusters = (int)std::max<int64_t>(1, total / cs);
+  // never more clusters than can be resident at once
+  for (;; cs >>= 1) {
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3((unsigned)(plan->nclusters * cs));
+    lc.blockDim = dim3((unsigned)plan->threads);
+    lc.dynamicSmemBytes = (size_t)plan->win_words * 4;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int active = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&active, k, &lc);
+    if (e == cudaSuccess && active > 0) {
+      plan->nclusters = std::min(plan->nclusters, active);
+      break;
+    }
+    cudaGetLastError();
+    if (cs == 1) return e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
+    plan->nclusters *= 2;                       // the same CTAs in half-size clusters
+  }
+  plan->cs = cs;
+  plan->nclusters = std::min(plan->nclusters, env_int("ESC_PAIR_CLUSTERS", plan->nclusters));
+  return cudaSuccess;
+}
+
+static cudaError_t launch_pairs_grp(bool big, const PairPlan& plan, const DevGraph& g, const int32_t* items,
+                                    int64_t nitems, unsigned long long* qctr, const TagScratch& ts,
+                                    const TriLists& tl3, const uint32_t* T, const AccSet& accs,
+                                    const PairTasks& pt, cudaStream_t s) {
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = plan.cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.gridDim = dim3((unsigned)(plan.nclusters * plan.cs));
+  lc.blockDim = dim3((unsigned)plan.threads);
+  lc.dynamicSmemBytes = (size_t)plan.win_words * 4;
+  lc.stream = s;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaErrorInvalidValue;
+#define ESC_PG(k, t, b)                                                                                   \
+  if (plan.shape == k)                                                                                    \
+    e = big ? cudaLaunchKernelEx(&lc, k_pairs_grp<true, t, b>, g, items, nitems, qctr, ts, tl3, T, accs, pt,     \
+                                 plan.wlo, plan.win_words)                                                      \
+            : cudaLaunchKernelEx(&lc, k_pairs_grp<false, t, b>, g, items, nitems, qctr, ts, tl3, T, accs, pt,    \
+                                 plan.wlo, plan.win_words);
+  ESC_PAIR_SHAPES(ESC_PG)
+#undef ESC_PG
+  note_launch();
+  return e;
+}
+
 cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, const CensusConfig& cfg,
                        unsigned long long* d_out, unsigned* d_status, PerElement* pe_out, Oriented* or_out,
                        cudaStream_t s) {
@@ -1744,21 +2204,34 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     ESC_TRY(cudaStreamSynchronize(s));   // nm lives on this stack frame
   }
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
+  // a census split over parts: the sweeps take the owned items only, and the
+  // sums of the phases every part repeats (degree sums, triangles) count on
+  // part 0 alone (the others add them to a discarded row)
+  const Owner own{cfg.part, std::max(1, cfg.parts)};
+  AccSet acc_rep = accs;
+  DevBuf b_junk;
+  if (own.part != 0) {
+    ESC_TRY(b_junk.alloc(sizeof(Acc128) * ACC_COUNT * G));
+    acc_rep.base = b_junk.as<Acc128>();
+  }
 
-  if (n > 0) (k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, accs), note_launch());
+  if (n > 0) (k_vertex_basic<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, acc_rep), note_launch());
 
   // ---------------- item lists for the out-neighbourhood passes
-  DevBuf b_small, b_large, b_wsmall, b_csmall, b_dims;
+  DevBuf b_small, b_large, b_wsmall, b_csmall, b_clarge, b_dims;
   ESC_TRY(b_small.alloc(sizeof(int32_t) * (n + 1)));
   ESC_TRY(b_large.alloc(sizeof(int32_t) * (n + 1)));
   ESC_TRY(b_wsmall.alloc(sizeof(int32_t) * (n + 1)));
   ESC_TRY(b_csmall.alloc(sizeof(int32_t) * (n + 1)));
+  ESC_TRY(b_clarge.alloc(sizeof(int32_t) * (n + 1)));
   ESC_TRY(b_dims.alloc(sizeof(unsigned long long) * 2));
   cudaMemsetAsync(b_dims.p, 0, sizeof(unsigned long long) * 2, s);
   if (n > 0) {
     (k_split_items<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), b_large.as<int32_t>(),
-                                                          b_wsmall.as<int32_t>(), b_csmall.as<int32_t>(), ctr,
-                                                          SMALL_DPLUS, CLQ_WARP_DIN), note_launch());
+                                                          b_wsmall.as<int32_t>(), b_csmall.as<int32_t>(),
+                                                          b_clarge.as<int32_t>(), ctr, SMALL_DPLUS,
+                                                          std::min(CLQ_WARP_DIN, env_int("ESC_CLQ_WARP_DIN", CLQ_WARP_DIN)),
+                                                          own), note_launch());
     (k_clique_dims<<<grid_for(n, TPB, sms), TPB, 0, s>>>(g, b_dims.as<unsigned long long>()), note_launch());
   }
   unsigned long long hcnt[16] = {0}, dims[2] = {0, 0};
@@ -1766,7 +2239,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   cudaMemcpyAsync(dims, b_dims.p, sizeof(dims), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
   int64_t nsmall = (int64_t)hcnt[0], nlarge = (int64_t)hcnt[1];
-  int64_t nwsmall = (int64_t)hcnt[2], ncsmall = (int64_t)hcnt[3];
+  int64_t nwsmall = (int64_t)hcnt[2], ncsmall = (int64_t)hcnt[3], nclarge = (int64_t)hcnt[4];
   int dmax = (int)dims[1];
   if (dmax < SMALL_DPLUS + 1) dmax = SMALL_DPLUS + 1;
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, s);
@@ -1777,11 +2250,12 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   size_t smem_a = sizeof(int32_t) * (2 * (size_t)hcap_a) + sizeof(uint32_t) * dmax;
   int grid_sweep = sms * (cfg.cta_per_sm > 0 ? cfg.cta_per_sm : 1);
   if (nsmall > 0)
-    (k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, accs), note_launch());
+    (k_tri_small<<<grid_for(nsmall * 32, TPB, sms), TPB, 0, s>>>(g, b_small.as<int32_t>(), nsmall, T, acc_rep),
+     note_launch());
   if (nlarge > 0) {
     if (smem_a > 48 * 1024) ESC_TRY(allow_max_smem((const void*)k_tri_large, smem_optin));
     (k_tri_large<<<(unsigned)std::min<int64_t>(grid_sweep, nlarge), 512, smem_a, s>>>(
-        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, accs, hcap_a), note_launch());
+        g, b_large.as<int32_t>(), nlarge, ctr + 0, T, acc_rep, hcap_a), note_launch());
   }
   if (n > 0) {
     (k_sym_T<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, tv), note_launch());
@@ -1796,23 +2270,25 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // pass B inputs
   // CTA items: every large out-neighbourhood, then the small ones with many
   // in-neighbours; the other small ones go to the warp kernel
-  int64_t nitems_b = nlarge + ncsmall;
+  int64_t nitems_b = nclarge + ncsmall;
   DevBuf b_items, b_D;
   ESC_TRY(b_items.alloc(sizeof(int32_t) * (nitems_b + 1)));
-  if (nlarge) cudaMemcpyAsync(b_items.p, b_large.p, sizeof(int32_t) * nlarge, cudaMemcpyDeviceToDevice, s);
+  if (nclarge) cudaMemcpyAsync(b_items.p, b_clarge.p, sizeof(int32_t) * nclarge, cudaMemcpyDeviceToDevice, s);
   if (ncsmall)
-    cudaMemcpyAsync(b_items.as<int32_t>() + nlarge, b_csmall.p, sizeof(int32_t) * ncsmall, cudaMemcpyDeviceToDevice,
+    cudaMemcpyAsync(b_items.as<int32_t>() + nclarge, b_csmall.p, sizeof(int32_t) * ncsmall, cudaMemcpyDeviceToDevice,
                     s);
-  int W_cap = (dmax + 63) >> 6;
-  int hcap_b = pow2_at_least(2 * dmax);
-  size_t smem_b = sizeof(uint64_t) * ((size_t)dmax * W_cap + dmax) + sizeof(int32_t) * (2 * (size_t)hcap_b) +
-                  sizeof(uint32_t) * dmax;
-  if (smem_b + 1024 > (size_t)smem_optin) return cudaErrorInvalidConfiguration;   // d+ beyond the bit matrix
-  ESC_TRY(allow_max_smem((const void*)k_clique_large, smem_optin));
+  // out-degrees up to dsplit keep the bit matrix in shared memory; the few
+  // larger ones (dense graphs) use a per-CTA region of global memory
+  int dsplit = dmax;
+  while (dsplit > SMALL_DPLUS + 1 && clique_space(dsplit) + 1024 > (size_t)smem_optin) --dsplit;
+  const int dmax_s = std::min(dmax, dsplit);
+  int hcap_b = pow2_at_least(2 * dmax_s);
+  size_t smem_b = clique_space(dmax_s);
+  ESC_TRY(allow_max_smem((const void*)k_clique_large<false>, smem_optin));
   // as many 256-thread CTAs per SM as registers and the bit matrix allow;
   // one 512-thread CTA per SM when fewer than two fit (large bit matrices)
   int clq_threads = 256, clq_per_sm = 1;
-  ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&clq_per_sm, k_clique_large, clq_threads, smem_b));
+  ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&clq_per_sm, k_clique_large<false>, clq_threads, smem_b));
   if (clq_per_sm < 2) {
     clq_threads = 512;
     clq_per_sm = 1;
@@ -1820,7 +2296,16 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   const int blocks_b = sms * std::min(clq_per_sm, 4);
   unsigned long long dwords = dims[0] > 0 ? dims[0] : 1;
   ESC_TRY(b_D.alloc(sizeof(uint64_t) * dwords * blocks_b));
-  CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords};
+  DevBuf b_Gq;
+  int blocks_g = 0;
+  int64_t gwords = 0;
+  if (dmax > dsplit) {
+    gwords = (int64_t)((clique_space(dmax) + 7) / 8);
+    // at most one CTA per SM, and at most 8 GiB of work space in all
+    blocks_g = (int)std::max<int64_t>(1, std::min<int64_t>(sms, ((int64_t)8 << 30) / (8 * gwords)));
+    ESC_TRY(b_Gq.alloc(sizeof(uint64_t) * (size_t)gwords * blocks_g));
+  }
+  CliqueScratch cs{b_D.as<uint64_t>(), (int64_t)dwords, b_Gq.as<uint64_t>(), gwords};
 
   // sweep scratch: one set per concurrent sweep (4-cycles; pairs and the
   // tagged 5-cycle counters are sized below, once the largest degree is known)
@@ -1848,6 +2333,22 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     cudaMemcpyAsync(&ulen, off + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&plen, offp + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   }
+  // pair-sweep items by wedge count (light / medium / heavy lists)
+  DevBuf b_plist, b_pctr;
+  ESC_TRY(b_plist.alloc(five ? sizeof(int32_t) * 3 * (size_t)(n + 1) : 16));
+  ESC_TRY(b_pctr.alloc(sizeof(unsigned long long) * 8));
+  cudaMemsetAsync(b_pctr.p, 0, sizeof(unsigned long long) * 8, s);
+  unsigned long long pcnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (five && n > 0) {
+    // item classes: hash capacities bound the light and medium classes
+    // (ESC_PAIR_SMALL_W / ESC_PAIR_LARGE_W lower them for tuning)
+    const long long w_small = std::min<long long>(PH_SMALL_W, env_int("ESC_PAIR_SMALL_W", PH_SMALL_W + 1) - 1);
+    const long long w_large = std::min<long long>(PH_LARGE_W, env_int("ESC_PAIR_LARGE_W", PH_LARGE_W + 1) - 1);
+    (k_pair_classify<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, b_plist.as<int32_t>(),
+                                                                b_pctr.as<unsigned long long>(), w_small,
+                                                                std::max(w_small, w_large), own), note_launch());
+    cudaMemcpyAsync(pcnt, b_pctr.p, sizeof(pcnt), cudaMemcpyDeviceToHost, s);
+  }
   std::vector<int64_t> hR(n + 1, 0);
   if (n > 0) cudaMemcpyAsync(hR.data(), o.R, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s);
   ESC_TRY(cudaStreamSynchronize(s));
@@ -1863,13 +2364,35 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] >= 65536) hi = mid; else lo = mid + 1; }
     jbig = lo;
   }
-  // the pair sweep: PAIR_CTAS_PER_SM persistent CTAs per SM unless the
-  // caller asked for a different count
-  const int grid_pairs = sms * (cfg.cta_per_sm == 2 ? PAIR_CTAS_PER_SM : std::max(1, cfg.cta_per_sm));
+  // the heavy pair items: clusters sharing one counter array each
+  PairPlan pplan;
+  if (five && pcnt[2] > 0) {
+    int64_t n0 = 0;                             // first rank of degree >= 1 (lower ranks are never counted)
+    {
+      int64_t lo = 0, hi = n;
+      while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] >= 1) hi = mid; else lo = mid + 1; }
+      n0 = lo;
+    }
+    size_t arr_bytes = sizeof(uint32_t) * (size_t)std::max<int64_t>(jbig - n0, 0) +
+                       sizeof(unsigned long long) * (size_t)(n - jbig);
+    ESC_TRY(plan_pair_clusters(jbig < n, sms, arr_bytes, n0, jbig, smem_optin, &pplan));
+  }
+  // task buffers of the heavy pair items: the largest item has at most
+  // w_max / PAIR_TASK + d_max tasks
+  DevBuf b_ptq, b_ptn;
+  PairTasks ptasks{nullptr, nullptr, 0};
+  if (five && pcnt[2] > 0) {
+    ptasks.cap = (int64_t)(pcnt[6] / PAIR_TASK) + maxdeg + 1;
+    ESC_TRY(b_ptq.alloc(sizeof(long long) * 2 * (size_t)ptasks.cap * pplan.nclusters));
+    ESC_TRY(b_ptn.alloc(sizeof(unsigned long long) * (size_t)pplan.nclusters));
+    cudaMemsetAsync(b_ptn.p, 0, sizeof(unsigned long long) * (size_t)pplan.nclusters, s);
+    ptasks.q = b_ptq.as<long long>();
+    ptasks.n = b_ptn.as<unsigned long long>();
+  }
   size_t sw32 = sizeof(uint32_t) * (size_t)jbig * grid_sweep + 16;
   size_t sw64 = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_sweep + 16;
-  size_t sw32p = five ? sizeof(uint32_t) * (size_t)jbig * grid_pairs + 16 : 16;
-  size_t sw64p = five ? sizeof(unsigned long long) * (size_t)(n - jbig) * grid_pairs + 16 : 16;
+  size_t sw32p = five ? sizeof(uint32_t) * (size_t)jbig * pplan.nclusters + 16 : 16;
+  size_t sw64p = five ? sizeof(unsigned long long) * (size_t)(n - jbig) * pplan.nclusters + 16 : 16;
   size_t sw32c = five ? sw32 : 16, sw64c = five ? sw64 : 16;
   DevBuf b_bigA, b_bigB, b_bigC;
   ESC_TRY(b_cntA.alloc(sw32)); ESC_TRY(b_bigA.alloc(sw64));
@@ -1896,8 +2419,11 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // wheel work items: ranks are in degree order, so the large centres are a suffix
   int64_t c0 = n;
   {
-    int64_t lo = 0, hi = n;                    // first rank with degree > WHEEL_WARP_MAX
-    while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] > WHEEL_WARP_MAX) hi = mid; else lo = mid + 1; }
+    // first rank with degree > the warp items' limit (WHEEL_WARP_MAX, or lower
+    // with ESC_WHEEL_WARP_MAX)
+    const int64_t wmax = std::min(WHEEL_WARP_MAX, env_int("ESC_WHEEL_WARP_MAX", WHEEL_WARP_MAX));
+    int64_t lo = 0, hi = n;
+    while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] > wmax) hi = mid; else lo = mid + 1; }
     c0 = lo;
   }
   DevBuf b_io, b_gs;
@@ -1910,7 +2436,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   std::vector<int64_t> item_off(n - c0 + 1, 0);
   if (five && c0 < n) {
     for (int64_t c = c0; c < n; ++c)
-      item_off[c - c0 + 1] = item_off[c - c0] + (hR[c + 1] - hR[c] + WHEEL_CHUNK - 1) / WHEEL_CHUNK;
+      item_off[c - c0 + 1] = item_off[c - c0] + (own.owns(c) ? (hR[c + 1] - hR[c] + WHEEL_CHUNK - 1) / WHEEL_CHUNK : 0);
     nitems_w = item_off[n - c0];
     ESC_TRY(b_io.alloc(sizeof(int64_t) * (n - c0 + 1)));
     cudaMemcpyAsync(b_io.p, item_off.data(), sizeof(int64_t) * (n - c0 + 1), cudaMemcpyHostToDevice, s);
@@ -1921,7 +2447,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   DevBuf b_wo;                                 // warp wheel items: offsets over centres c0-1 .. 0
   if (five && c0 > 0) {
     ESC_TRY(b_wo.alloc(sizeof(int64_t) * (size_t)(c0 + 1)));
-    (k_wheel_warp_counts<<<grid_for(c0, TPB, sms), TPB, 0, s>>>(g, c0, b_wo.as<int64_t>()), note_launch());
+    (k_wheel_warp_counts<<<grid_for(c0, TPB, sms), TPB, 0, s>>>(g, c0, b_wo.as<int64_t>(), own), note_launch());
     ESC_TRY(exclusive_scan_i64(b_wo.as<int64_t>(), b_wo.as<int64_t>(), c0, true, arena, s));
   }
 
@@ -1958,20 +2484,42 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // pairs (Thms 11, 12); 16-bit counters when no degree reaches 2^16 (then no W(i,j) can)
   mark(5, 0, s);
   if (five && n > 0) {
-    // 16-bit counters when no degree reaches 2^16 (then no W(i,j) can);
-    // whole warps only: the kernel's reductions shuffle across full warps
-    int pthreads = cfg.cta_per_sm == 2 ? 512 : std::max(128, std::min(512, (1024 / std::max(1, cfg.cta_per_sm)) & ~31));
-    if (jbig < n)
-      (k_pairs<true><<<grid_pairs, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
-    else
-      (k_pairs<false><<<grid_pairs, pthreads, 0, s>>>(g, ctr + 4, 0, n, tsB, tl3, T, accs), note_launch());
+    unsigned long long* pq = b_pctr.as<unsigned long long>() + 3;     // queue counters of the three lists
+    const int32_t* pl = b_plist.as<int32_t>();
+    if (pcnt[0] > 0) {
+      const size_t sm0 = (sizeof(int32_t) + sizeof(uint32_t)) * PH_SMALL_SLOTS;
+      int per_sm = 1;
+      ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_hash<PH_SMALL_SLOTS>, PH_SMALL_THREADS,
+                                                            sm0));
+      unsigned grid = (unsigned)std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, (int64_t)pcnt[0]);
+      (k_pairs_hash<PH_SMALL_SLOTS><<<grid, PH_SMALL_THREADS, sm0, s>>>(g, pl, (int64_t)pcnt[0], pq + 0, tl3, T, accs,
+                                                                       d_status), note_launch());
+    }
+    if (pcnt[1] > 0) {
+      const size_t sm1 = (sizeof(int32_t) + sizeof(uint32_t)) * PH_LARGE_SLOTS;
+      ESC_TRY(allow_max_smem((const void*)k_pairs_hash<PH_LARGE_SLOTS>, smem_optin));
+      int per_sm = 1;
+      ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_hash<PH_LARGE_SLOTS>, PH_LARGE_THREADS,
+                                                            sm1));
+      unsigned grid = (unsigned)std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, (int64_t)pcnt[1]);
+      (k_pairs_hash<PH_LARGE_SLOTS><<<grid, PH_LARGE_THREADS, sm1, s>>>(g, pl + n, (int64_t)pcnt[1], pq + 1, tl3, T,
+                                                                       accs, d_status), note_launch());
+    }
+    if (pcnt[2] > 0)
+      ESC_TRY(launch_pairs_grp(jbig < n, pplan, g, pl + 2 * n, (int64_t)pcnt[2], pq + 2, tsB, tl3, T, accs, ptasks,
+                               s));
   }
   mark(5, 1, s);
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)
   mark(2, 0, s1);
   if (nitems_b > 0)
-    (k_clique_large<<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), clq_threads, smem_b, s1>>>(
-        g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, dmax, d_status, five), note_launch());
+    (k_clique_large<false><<<(unsigned)std::min<int64_t>(blocks_b, nitems_b), clq_threads, smem_b, s1>>>(
+        g, b_items.as<int32_t>(), nitems_b, ctr + 1, T, K4e, accs, cs, hcap_b, -1, dmax_s, d_status, five),
+     note_launch());
+  if (nitems_b > 0 && blocks_g > 0)
+    (k_clique_large<true><<<(unsigned)std::min<int64_t>(blocks_g, nitems_b), 512, 0, s1>>>(
+        g, b_items.as<int32_t>(), nitems_b, ctr + 9, T, K4e, accs, cs, pow2_at_least(2 * dmax), dsplit, dmax,
+        d_status, five), note_launch());
   if (nwsmall > 0) {
     int per_sm = 1;
     ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_warp, CLQ_WARPS * 32, 0));
@@ -1981,16 +2529,17 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   }
   if (n > 0) {
     (k_sym_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e), note_launch());
-    (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e, K4v, 3), note_launch());
+    if (!cfg.partial)                          // a part's K4 sums are divided once every part's are in
+      (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s1>>>(g, K4e, K4v, 3), note_launch());
   }
   mark(2, 1, s1);
   // 4-cycles (Thm 5)
   mark(3, 0, s2);
   if (n > 0) {
     if (jbig < n)
-      (k_cycles4<true><<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, tsA, C4e, C4v, accs), note_launch());
+      (k_cycles4<true><<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, tsA, C4e, C4v, accs, own), note_launch());
     else
-      (k_cycles4<false><<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, tsA, C4e, C4v, accs), note_launch());
+      (k_cycles4<false><<<grid_sweep, 512, 0, s2>>>(g, ctr + 2, tsA, C4e, C4v, accs, own), note_launch());
     (k_fold_u64<<<grid_for(n * 32, TPB, sms), TPB, 0, s2>>>(g, C4e), note_launch());
   }
   mark(3, 1, s2);
@@ -1998,23 +2547,29 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(7, 0, s4);
   if (five && n > 0) {
     if (jbig < n)
-      (k_cycles5<true><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs), note_launch());
+      (k_cycles5<true><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs, own), note_launch());
     else
-      (k_cycles5<false><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs), note_launch());
+      (k_cycles5<false><<<grid_sweep, 512, 0, s4>>>(g, ctr + 6, tsC, ssC, accs, own), note_launch());
   }
   mark(7, 1, s4);
   ESC_TRY(ss_all.join_into(s));
 
   // ---------------- closed forms over vertices and edges, then assembly
   mark(8, 0, s);
-  if (n > 0)
-    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, accs), note_launch());
-  ConvTables tabs;
-  conversion_inverse(3, tabs.a3);
-  conversion_inverse(4, tabs.a4);
-  conversion_inverse(5, tabs.a5);
-  (k_assemble<<<(G + 63) / 64, 64, 0, s>>>(acc, b_narr.as<unsigned long long>(), b_marr.as<unsigned long long>(), G,
-                                          tabs, d_out), note_launch());
+  if (cfg.partial) {
+    // one part of a split census: its raw sums; the closed forms need every
+    // part's per-element counts and run in run_census_finish
+    ESC_TRY(cudaMemcpyAsync(cfg.d_acc_out, acc, sizeof(Acc128) * ACC_COUNT, cudaMemcpyDeviceToDevice, s));
+  } else {
+    if (n > 0)
+      (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, C4e, K4e, tv, C4v, K4v, accs), note_launch());
+    ConvTables tabs;
+    conversion_inverse(3, tabs.a3);
+    conversion_inverse(4, tabs.a4);
+    conversion_inverse(5, tabs.a5);
+    (k_assemble<<<(G + 63) / 64, 64, 0, s>>>(acc, b_narr.as<unsigned long long>(), b_marr.as<unsigned long long>(),
+                                            G, tabs, d_out, (u128*)cfg.d_basis), note_launch());
+  }
   mark(8, 1, s);
 
   if (pe_out) {
@@ -2033,5 +2588,38 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   ESC_TRY(cudaStreamSynchronize(s));   // scratch buffers are freed on return
   return cudaGetLastError();
 }
+
+// The end of a split census: every part's sums added (d_acc, ACC_COUNT
+// 128-bit words) and every part's per-element counts added into pe (K4e, C4e,
+// C4v; T and tv are whole on every part).  K4 per vertex, the closed forms
+// over vertices and edges, and the assembly.
+cudaError_t run_census_finish(const Oriented& o, int64_t n, int64_t nnz, const PerElement& pe,
+                              const unsigned long long* d_acc, unsigned long long* d_out, int sms, cudaStream_t s) {
+  CacheScope cache_scope(s);
+  const int TPB = 256;
+  DevGraph g{n, nnz, o.R, o.C, o.op, o.rev};
+  DevBuf b_acc, b_nm;
+  ESC_TRY(b_acc.alloc(sizeof(Acc128) * ACC_COUNT));
+  ESC_TRY(b_nm.alloc(sizeof(unsigned long long) * 2));
+  ESC_TRY(cudaMemcpyAsync(b_acc.p, d_acc, sizeof(Acc128) * ACC_COUNT, cudaMemcpyDeviceToDevice, s));
+  unsigned long long nm[2] = {(unsigned long long)n, (unsigned long long)(nnz / 2)};
+  ESC_TRY(cudaMemcpyAsync(b_nm.p, nm, sizeof(nm), cudaMemcpyHostToDevice, s));
+  AccSet accs{b_acc.as<Acc128>(), nullptr};
+  if (n > 0) {
+    (k_vertex_sum_div<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, pe.K4e, pe.K4v, 3), note_launch());
+    (k_edge_sums<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, pe.Te, pe.C4e, pe.K4e, pe.tv, pe.C4v, pe.K4v, accs),
+     note_launch());
+  }
+  ConvTables tabs;
+  conversion_inverse(3, tabs.a3);
+  conversion_inverse(4, tabs.a4);
+  conversion_inverse(5, tabs.a5);
+  (k_assemble<<<1, 64, 0, s>>>(b_acc.as<Acc128>(), b_nm.as<unsigned long long>(), b_nm.as<unsigned long long>() + 1,
+                               1, tabs, d_out, nullptr), note_launch());
+  ESC_TRY(cudaStreamSynchronize(s));   // nm lives on this stack frame
+  return cudaGetLastError();
+}
+
+int census_sum_count() { return ACC_COUNT; }
 
 }  // namespace esc

@@ -32,6 +32,8 @@ enum AccId {
   ACC_D2D,        // sum_c C(d_c,2) d_c
   ACC_DNBR,       // sum_c (d_c-1) sum_{a in N(c)} d_a
   ACC_TD,         // sum_i t_i d_i
+  ACC_DP,         // sum over out-edges a -> b of (d+(a) - 1) d+(b)   directed 3-paths i <- a -> b -> j
+  ACC_DBP,        // sum over directed triangles of C(apexes above, 2)  directed bipyramids
   ACC_COUNT
 };
 
@@ -212,6 +214,26 @@ enum DevErr : unsigned {
 };
 
 __device__ __forceinline__ void set_err(unsigned* st, unsigned bit) { atomicOr(st, bit); }
+
+// ---------------------------------------------------------------- ownership
+// When one census is split over `parts` processes (each holding the whole
+// graph), work item i -- a vertex rank -- belongs to part i mod parts.  Ranks
+// are in degree order, so every part gets the same mix of heavy and light
+// items.  Items are taken from the top rank down.
+struct Owner {
+  int part = 0, parts = 1;
+  __host__ __device__ bool owns(int64_t i) const { return parts <= 1 || i % parts == part; }
+  __host__ __device__ int64_t top(int64_t n) const {      // highest owned rank, or -1
+    if (n <= 0) return -1;
+    int64_t t = n - 1 - ((n - 1 - part) % parts + parts) % parts;
+    return t >= part ? t : -1;
+  }
+  __host__ __device__ int64_t count(int64_t n) const {
+    int64_t t = top(n);
+    return t < 0 ? 0 : (t - part) / parts + 1;
+  }
+  __host__ __device__ int64_t item(int64_t n, int64_t it) const { return top(n) - it * parts; }
+};
 
 // ---------------------------------------------------------------- work queue
 // Persistent CTAs pull vertex indices from `order` (vertices sorted by

@@ -22,6 +22,9 @@ struct escape_graph {
   float phase_ms[9] = {0};
   int num_phases = 0;
   long long launches = 0;     // kernels launched by the last census call
+  escape_u128 basis[4] = {};  // W, D, DP, DBP of the last census5 call
+  bool has_basis = false;
+  bool has_part = false;      // a part of a split census is held (pe, ori)
 };
 
 namespace {
@@ -258,7 +261,7 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
                          float* phase_ms, int* nphase, bool four_only = false) {
   unsigned long long* d_out = nullptr;
   unsigned* d_status = nullptr;
-  cudaError_t e = cudaMalloc(&d_out, sizeof(escape_census));
+  cudaError_t e = cudaMalloc(&d_out, sizeof(escape_census) + sizeof(escape_u128) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
   if (e != cudaSuccess) { cudaFree(d_out); return from_cuda(e); }
   cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
@@ -275,18 +278,25 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
   cfg.phase_events = nev ? evs : nullptr;
   cfg.num_phase_events = nev;
   cfg.four_only = four_only;
+  cfg.d_basis = d_out + sizeof(escape_census) / sizeof(unsigned long long);
   e = esc::run_census(d_rp, d_col, n, nnz, cfg, d_out, d_status, keep ? pe : nullptr,
                       keep ? ori : nullptr, s);
   escape_status st = from_cuda(e);
   unsigned hstat = 0;
   if (st == ESCAPE_OK) {
     escape_census tmp;
+    escape_u128 basis[4];
     e = cudaMemcpyAsync(&tmp, d_out, sizeof(escape_census), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(basis, cfg.d_basis, sizeof(basis), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     st = from_cuda(e);
     if (st == ESCAPE_OK && hstat != 0) st = ESCAPE_EINTERNAL;
-    if (st == ESCAPE_OK) *out = tmp;
+    if (st == ESCAPE_OK) {
+      *out = tmp;
+      for (int i = 0; i < 4; ++i) g->basis[i] = basis[i];
+      g->has_basis = !four_only;
+    }
   }
   if (nev) {
     int phases = 0;
@@ -417,6 +427,8 @@ escape_status escape_census5(escape_graph* g, escape_census* out, void* stream) 
   if (!g || !out) return ESCAPE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   free_pe(g);
+  g->has_basis = false;
+  g->has_part = false;
   long long l0 = esc::launches_so_far();
   escape_status st = census_one(g, g->d_rp, g->d_col, g->n, g->nnz, out, s, g->keep_pe != 0, &g->pe, &g->ori,
                                 g->phase_ms, &g->num_phases);
@@ -430,6 +442,8 @@ escape_status escape_census4(escape_graph* g, escape_census34* out, void* stream
   if (!g || !out) return ESCAPE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   free_pe(g);
+  g->has_basis = false;
+  g->has_part = false;
   long long l0 = esc::launches_so_far();
   escape_census full;
   escape_status st = census_one(g, g->d_rp, g->d_col, g->n, g->nnz, &full, s, g->keep_pe != 0, &g->pe, &g->ori,
@@ -444,40 +458,15 @@ escape_status escape_census4(escape_graph* g, escape_census34* out, void* stream
   return st;
 }
 
-escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offsets, const int64_t* row_ptr,
-                                   const int32_t* col, uint32_t flags, escape_census* out, void* stream) {
-  if (num_graphs < 0 || (num_graphs > 0 && (!vtx_offsets || !row_ptr || !out))) return ESCAPE_EINVAL;
-  if (num_graphs == 0) return ESCAPE_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  bool dev_ptrs = (flags & ESCAPE_DEVICE_PTRS) != 0;
+// One chunk of a batch: G graphs whose vertex offsets voff (G + 1) and row
+// pointer rp (rows + 1) are host arrays starting at 0, and whose entries are
+// col[0 .. rp[rows]) (host or device memory).
+static escape_status batch_chunk(int32_t num_graphs, const int64_t* voff_h, const int64_t* rp_h, const int32_t* col,
+                                 bool dev_ptrs, uint32_t flags, escape_census* out, cudaStream_t s, int sms) {
+  const int64_t rows = voff_h[num_graphs];
+  int64_t nnz = rp_h[rows];
   cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int sms = device_sms(dev);
-  // sizes on the host: the vertex offsets and the total entry count
-  std::vector<int64_t> voff(num_graphs + 1);
   cudaError_t e = cudaSuccess;
-  if (dev_ptrs) e = cudaMemcpyAsync(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, s);
-  else memcpy(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1));
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return from_cuda(e);
-  if (voff[0] != 0) return ESCAPE_EINVAL;
-  for (int k = 0; k < num_graphs; ++k)
-    if (voff[k + 1] < voff[k] || voff[k + 1] - voff[k] > 2147483647LL) return ESCAPE_EINVAL;
-  int64_t rows = voff[num_graphs];
-  if (rows > 2147483647LL) return ESCAPE_EOVERFLOW;      // the union is one graph of int32 ids
-  // every row offset is checked on the host before any kernel indexes col
-  // through it (device input is copied here first)
-  std::vector<int64_t> hrp;
-  const int64_t* h = row_ptr;
-  if (dev_ptrs) {
-    e = fetch_row_ptr(row_ptr, rows, hrp, s);
-    if (e != cudaSuccess) return from_cuda(e);
-    h = hrp.data();
-  }
-  if (!row_ptr_ok(h, rows, -1)) return ESCAPE_EINVAL;
-  int64_t nnz = h[rows];
-  if (nnz > 0 && !col) return ESCAPE_EINVAL;
   // device copies: offsets, rows, entries turned into union ids
   int64_t *d_voff = nullptr, *d_rp = nullptr;
   int32_t* d_col = nullptr;
@@ -488,8 +477,8 @@ escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offset
   if (e == cudaSuccess) e = cudaMalloc(&d_col, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(escape_census) * num_graphs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_voff, voff.data(), sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (rows + 1), kind, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_voff, voff_h, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp_h, sizeof(int64_t) * (rows + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, kind, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
   escape_status st = from_cuda(e);
@@ -544,6 +533,80 @@ escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offset
   return st;
 }
 
+
+escape_status escape_census5_batch(int32_t num_graphs, const int64_t* vtx_offsets, const int64_t* row_ptr,
+                                   const int32_t* col, uint32_t flags, escape_census* out, void* stream) {
+  if (num_graphs < 0 || (num_graphs > 0 && (!vtx_offsets || !row_ptr || !out))) return ESCAPE_EINVAL;
+  if (num_graphs == 0) return ESCAPE_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool dev_ptrs = (flags & ESCAPE_DEVICE_PTRS) != 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = device_sms(dev);
+  // sizes on the host: the vertex offsets and the total entry count
+  std::vector<int64_t> voff(num_graphs + 1);
+  cudaError_t e = cudaSuccess;
+  if (dev_ptrs) e = cudaMemcpyAsync(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1), cudaMemcpyDeviceToHost, s);
+  else memcpy(voff.data(), vtx_offsets, sizeof(int64_t) * (num_graphs + 1));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (voff[0] != 0) return ESCAPE_EINVAL;
+  for (int k = 0; k < num_graphs; ++k)
+    if (voff[k + 1] < voff[k] || voff[k + 1] - voff[k] > 2147483647LL) return ESCAPE_EINVAL;
+  int64_t rows = voff[num_graphs];
+  if (rows > 2147483647LL) return ESCAPE_EOVERFLOW;      // the union is one graph of int32 ids
+  // every row offset is checked on the host before any kernel indexes col
+  // through it (device input is copied here first)
+  std::vector<int64_t> hrp;
+  const int64_t* h = row_ptr;
+  if (dev_ptrs) {
+    e = fetch_row_ptr(row_ptr, rows, hrp, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    h = hrp.data();
+  }
+  if (!row_ptr_ok(h, rows, -1)) return ESCAPE_EINVAL;
+  int64_t nnz = h[rows];
+  if (nnz > 0 && !col) return ESCAPE_EINVAL;
+  // Chunks of consecutive graphs, each counted as one block-diagonal union,
+  // sized so that a chunk's work space stays within about half of the free
+  // device memory (at most 64 GiB): per graph the common-neighbour lists
+  // (36 B per triangle, and 3T <= W), per-entry and per-vertex arrays, and per
+  // union vertex the sweeps' per-CTA counters.
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  double budget = std::min((double)free_b * 0.5, (double)((size_t)64 << 30));
+  if (const char* v = getenv("ESC_BATCH_CHUNK_MB"))          // a smaller chunk budget (tests, tuning)
+    if (atof(v) > 0) budget = std::min(budget, atof(v) * (1 << 20));
+  std::vector<int64_t> vrb, rrb;
+  int32_t k0 = 0;
+  while (k0 < num_graphs) {
+    int32_t k1 = k0;
+    double used = 0;
+    while (k1 < num_graphs) {
+      double wedges = 0;
+      for (int64_t r = voff[k1]; r < voff[k1 + 1]; ++r) {
+        double d = (double)(h[r + 1] - h[r]);
+        wedges += d * (d - 1) / 2;
+      }
+      const double nk = (double)(voff[k1 + 1] - voff[k1]), ek = (double)(h[voff[k1 + 1]] - h[voff[k1]]);
+      const double need = 12.0 * wedges + 160.0 * ek + 200.0 * nk + 32.0 * 4 * sms * nk;
+      if (k1 > k0 && used + need > budget) break;
+      used += need;
+      ++k1;
+    }
+    // the chunk's offsets and rows, starting at 0
+    const int64_t r0 = voff[k0], r1 = voff[k1], e0 = h[r0];
+    vrb.resize((size_t)(k1 - k0) + 1);
+    for (int32_t k = k0; k <= k1; ++k) vrb[k - k0] = voff[k] - r0;
+    rrb.resize((size_t)(r1 - r0) + 1);
+    for (int64_t r = r0; r <= r1; ++r) rrb[r - r0] = h[r] - e0;
+    escape_status st = batch_chunk(k1 - k0, vrb.data(), rrb.data(), col ? col + e0 : nullptr, dev_ptrs, flags,
+                                   out + k0, s, sms);
+    if (st != ESCAPE_OK) return st;
+    k0 = k1;
+  }
+  return ESCAPE_OK;
+}
 escape_status escape_per_element(escape_graph* g, uint64_t* tri_e, uint64_t* c4_e, uint64_t* k4_e, uint64_t* tri_v,
                                  uint64_t* c4_v, uint64_t* k4_v, void* stream) {
   if (!g || !g->has_pe) return ESCAPE_EINVAL;
@@ -582,6 +645,105 @@ int escape_last_phase_ms(const escape_graph* g, float* ms, int count) {
 }
 
 long long escape_last_kernel_launches(const escape_graph* g) { return g ? g->launches : 0; }
+
+int escape_part_sum_count(void) { return esc::census_sum_count(); }
+
+escape_status escape_census5_part(escape_graph* g, int32_t part, int32_t parts, escape_part* out, void* stream) {
+  if (!g || !out || parts < 1 || part < 0 || part >= parts) return ESCAPE_EINVAL;
+  if (esc::census_sum_count() > ESCAPE_PART_SUMS) return ESCAPE_EOVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  free_pe(g);
+  g->has_basis = false;
+  g->has_part = false;
+  long long l0 = esc::launches_so_far();
+  unsigned long long *d_acc = nullptr, *d_out = nullptr;
+  unsigned* d_status = nullptr;
+  const int nsum = esc::census_sum_count();
+  cudaError_t e = cudaMalloc(&d_acc, sizeof(escape_u128) * nsum);
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(escape_census));
+  if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
+  escape_status st = from_cuda(e);
+  if (st == ESCAPE_OK) {
+    esc::CensusConfig cfg;
+    cfg.sms = g->sms;
+    cfg.cta_per_sm = g->cta_per_sm;
+    cfg.keep_per_element = true;
+    cfg.serial_phases = g->serial > 0 || (g->serial < 0 && g->nnz >= ((int64_t)1 << 24));
+    cfg.part = part;
+    cfg.parts = parts;
+    cfg.partial = true;
+    cfg.d_acc_out = d_acc;
+    st = from_cuda(esc::run_census(g->d_rp, g->d_col, g->n, g->nnz, cfg, d_out, d_status, &g->pe, &g->ori, s));
+  }
+  if (st == ESCAPE_OK) {
+    escape_part tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    unsigned h = 0;
+    e = cudaMemcpyAsync(tmp.sums, d_acc, sizeof(escape_u128) * nsum, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = from_cuda(e);
+    if (st == ESCAPE_OK && h) st = ESCAPE_EINTERNAL;
+    if (st == ESCAPE_OK) *out = tmp;
+  }
+  cudaFree(d_acc);
+  cudaFree(d_out);
+  cudaFree(d_status);
+  g->launches = esc::launches_so_far() - l0;
+  if (st == ESCAPE_OK) g->has_part = true;
+  else free_pe(g);
+  return st;
+}
+
+escape_status escape_part_counts(escape_graph* g, uint64_t* k4_e, uint64_t* c4_e, uint64_t* c4_v, uint32_t flags,
+                                 void* stream) {
+  if (!g || !g->has_part) return ESCAPE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dev = (flags & ESCAPE_DEVICE_PTRS) != 0, put = (flags & ESCAPE_PART_PUT) != 0;
+  cudaMemcpyKind kind = put ? (dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                            : (dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  uint64_t* mine[3] = {(uint64_t*)g->pe.K4e, (uint64_t*)g->pe.C4e, (uint64_t*)g->pe.C4v};
+  uint64_t* theirs[3] = {k4_e, c4_e, c4_v};
+  const int64_t len[3] = {g->nnz, g->nnz, g->n};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    if (!theirs[k] || len[k] == 0) continue;
+    e = put ? cudaMemcpyAsync(mine[k], theirs[k], sizeof(uint64_t) * len[k], kind, s)
+            : cudaMemcpyAsync(theirs[k], mine[k], sizeof(uint64_t) * len[k], kind, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+escape_status escape_census5_finish(escape_graph* g, const escape_part* total, escape_census* out, void* stream) {
+  if (!g || !total || !out || !g->has_part) return ESCAPE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  long long l0 = esc::launches_so_far();
+  unsigned long long *d_acc = nullptr, *d_out = nullptr;
+  const int nsum = esc::census_sum_count();
+  cudaError_t e = cudaMalloc(&d_acc, sizeof(escape_u128) * nsum);
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(escape_census));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_acc, total->sums, sizeof(escape_u128) * nsum, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = esc::run_census_finish(g->ori, g->n, g->nnz, g->pe, d_acc, d_out, g->sms, s);
+  escape_census tmp;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&tmp, d_out, sizeof(escape_census), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  escape_status st = from_cuda(e);
+  if (st == ESCAPE_OK) *out = tmp;
+  cudaFree(d_acc);
+  cudaFree(d_out);
+  g->launches = esc::launches_so_far() - l0;
+  free_pe(g);
+  g->has_part = false;
+  return st;
+}
+
+escape_status escape_last_basis_counts(const escape_graph* g, escape_u128* out) {
+  if (!g || !out || !g->has_basis) return ESCAPE_EINVAL;
+  for (int i = 0; i < 4; ++i) out[i] = g->basis[i];
+  return ESCAPE_OK;
+}
 
 void escape_free(escape_graph* g) {
   if (!g) return;

@@ -86,11 +86,29 @@ struct CensusConfig {
   // then receives num_graphs results
   const int64_t* d_vtx_offsets = nullptr;
   int num_graphs = 1;
+  // optional device output: per graph W, D, directed 3-paths, directed
+  // bipyramids (4 x u128, two little-endian words each)
+  unsigned long long* d_basis = nullptr;
+  // a census split over `parts` processes: this call counts the items of
+  // `part` (vertex ranks i with i mod parts = part) and, with `partial`, stops
+  // before the closed forms, writing its raw sums (census_sum_count() u128)
+  // to d_acc_out and keeping the per-element arrays (pe_out, or_out required)
+  int part = 0, parts = 1;
+  bool partial = false;
+  unsigned long long* d_acc_out = nullptr;
 };
 
 cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz, const CensusConfig& cfg,
                        unsigned long long* d_out, unsigned* d_status, PerElement* pe_out, Oriented* or_out,
                        cudaStream_t s);
+
+// The end of a split census (see CensusConfig::partial): d_acc holds every
+// part's raw sums added, pe every part's per-element counts added.
+cudaError_t run_census_finish(const Oriented& o, int64_t n, int64_t nnz, const PerElement& pe,
+                              const unsigned long long* d_acc, unsigned long long* d_out, int sms, cudaStream_t s);
+
+// Number of raw 128-bit sums of one part of a split census.
+int census_sum_count();
 
 // Conversion tables (App. B), built on the host by this library's own
 // embedding count over the pattern catalogue.

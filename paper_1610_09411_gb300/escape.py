@@ -20,6 +20,8 @@ from . import build as _build
 ESCAPE_HOST_PTRS = 0
 ESCAPE_DEVICE_PTRS = 1
 ESCAPE_NORMALIZE = 2
+ESCAPE_PART_PUT = 4
+ESCAPE_PART_SUMS = 64
 
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EOVERFLOW", 5: "ETIMEOUT", 6: "EINTERNAL"}
 N_PHASES = 9
@@ -79,6 +81,16 @@ def _load():
     lib.escape_last_phase_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), c_int]
     lib.escape_last_kernel_launches.restype = ctypes.c_longlong
     lib.escape_last_kernel_launches.argtypes = [P]
+    lib.escape_census5_part.restype = c_int
+    lib.escape_census5_part.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P]
+    lib.escape_part_counts.restype = c_int
+    lib.escape_part_counts.argtypes = [P, P, P, P, u32, P]
+    lib.escape_census5_finish.restype = c_int
+    lib.escape_census5_finish.argtypes = [P, P, ctypes.POINTER(Census), P]
+    lib.escape_part_sum_count.restype = c_int
+    lib.escape_part_sum_count.argtypes = []
+    lib.escape_last_basis_counts.restype = c_int
+    lib.escape_last_basis_counts.argtypes = [P, P]
     lib.escape_cycles4_noalloc.restype = c_int
     lib.escape_cycles4_noalloc.argtypes = [i64, P, P, P, P, P]
     lib.escape_free.restype = None
@@ -213,6 +225,59 @@ def escape_last_phase_ms(h) -> dict:
 
 def escape_last_kernel_launches(h) -> int:
     return int(LIB.escape_last_kernel_launches(h))
+
+
+class Part(ctypes.Structure):
+    _fields_ = [("sums", U128 * ESCAPE_PART_SUMS)]
+
+
+def escape_part_sum_count() -> int:
+    return int(LIB.escape_part_sum_count())
+
+
+def escape_census5_part(h, part: int, parts: int, stream=None) -> list:
+    """This part's raw sums of a census split over `parts` (Python ints, the
+    first escape_part_sum_count() entries)."""
+    out = Part()
+    _check(LIB.escape_census5_part(h, int(part), int(parts), ctypes.byref(out), _stream(stream)),
+           "escape_census5_part")
+    k = escape_part_sum_count()
+    return [int(out.sums[i].lo) | (int(out.sums[i].hi) << 64) for i in range(k)]
+
+
+def escape_part_counts(h, k4_e=None, c4_e=None, c4_v=None, put: bool = False, stream=None):
+    """Read (or, with put, write) the part's per-element arrays: uint64/int64
+    numpy arrays or torch CUDA tensors of nnz, nnz and n entries."""
+    ptrs = [_ptr(a) for a in (k4_e, c4_e, c4_v)]
+    devs = {d for p, d in ptrs if p is not None}
+    if len(devs) > 1:
+        raise ValueError("arrays must all be host or all be device arrays")
+    flags = (ESCAPE_DEVICE_PTRS if devs == {True} else 0) | (ESCAPE_PART_PUT if put else 0)
+    _check(LIB.escape_part_counts(h, ptrs[0][0], ptrs[1][0], ptrs[2][0], flags, _stream(stream)),
+           "escape_part_counts")
+
+
+def escape_census5_finish(h, total_sums, stream=None) -> dict:
+    """The census from every part's sums added (modulo 2^128) and the handle's
+    per-element arrays holding every part's counts added."""
+    tot = Part()
+    mask = (1 << 64) - 1
+    for i, v in enumerate(total_sums):
+        v %= 1 << 128
+        tot.sums[i].lo = v & mask
+        tot.sums[i].hi = v >> 64
+    out = Census()
+    _check(LIB.escape_census5_finish(h, ctypes.byref(tot), ctypes.byref(out), _stream(stream)),
+           "escape_census5_finish")
+    return out.to_dict()
+
+
+def escape_last_basis_counts(h) -> dict:
+    """W, D, DP, DBP of the last escape_census5 call on the handle (Python ints)."""
+    out = (U128 * 4)()
+    _check(LIB.escape_last_basis_counts(h, out), "escape_last_basis_counts")
+    vals = [int(x.lo) | (int(x.hi) << 64) for x in out]
+    return dict(zip(("W", "D", "DP", "DBP"), vals))
 
 
 def escape_cycles4_noalloc(n: int, row_ptr, col, c4_v, c4_total, stream=None):

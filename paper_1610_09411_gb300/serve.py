@@ -11,6 +11,11 @@ request that arrives while others are being counted joins the next batch.
 Each result is the same as the graph's census alone: the batched pass keeps a
 separate exact accumulator row per graph.
 
+Batches are also capped by predicted GPU time: every request carries the
+census time the run-time model (predict.py, the paper's fit of run time to
+basis counts, here from counts of the CSR) predicts for it, and a batch stops
+growing at max_batch_seconds of predicted work.
+
 The execution step is injectable (``run_batch``) so the admission and
 batching logic can be exercised without a GPU.
 """
@@ -24,21 +29,46 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .predict import Predictor, host_counts
 
-def footprint_bytes(n: int, m: int, sms: int = 152, cta_per_sm: int = 2) -> int:
+
+def triangle_bound(row_ptr: np.ndarray, col: np.ndarray) -> int:
+    """Upper bound on the triangle count T from the degrees alone: an edge
+    {u, v} lies in at most min(d_u, d_v) - 1 triangles and every triangle has
+    three edges, so 3T <= sum over edges of (min(d_u, d_v) - 1)."""
+    n = len(row_ptr) - 1
+    if n <= 0 or len(col) == 0:
+        return 0
+    deg = np.diff(row_ptr).astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    per_entry = np.minimum(deg[src], deg[col.astype(np.int64)]) - 1   # each edge appears twice
+    return int(per_entry.clip(min=0).sum()) // 6
+
+
+def footprint_bytes(n: int, m: int, tri_bound: int | None = None, max_deg: int | None = None,
+                    sms: int = 152, cta_per_sm: int = 2) -> int:
     """Conservative device bytes for the census of one graph (n vertices, m
-    edges): the CSR and its renamed copy, per-edge arrays and common-neighbour
-    lists (bounded by the edge count times a triangle factor), and the sweep
-    scratch that grows with n: per persistent CTA, 4 B per vertex for each of
-    the tagged 4-cycle, pair and 5-cycle counters (the pair sweep runs three
-    CTAs per SM), 8 B for the 5-cycle P2 counters and their list, and 8 B for
-    the wheel counters of large centres (their degree is at most n).  Used for
-    admission only."""
+    edges, at most tri_bound triangles, largest degree max_deg): the CSR and
+    its renamed copy and per-edge arrays; the common-neighbour lists, 3T ids
+    and 6T positions (36 B per triangle); and the sweep scratch: per vertex, 8 B
+    for each persistent CTA of the 4-cycle and 5-cycle sweeps (tagged counters)
+    plus 8 B for the 5-cycle P2 counters and their list, 8 B per CTA slot of
+    the pair sweep's counter arrays; per unit of the largest degree, the
+    per-CTA wheel counters and common-neighbour hash tables.  Without a
+    triangle bound, the lists are charged as if every edge were in max_deg
+    triangles.  Used for admission only; the library's cache of released
+    buffers (up to 8 GiB) and its fixed 8 MiB no-allocation array are not
+    part of it."""
     nnz = 2 * m
+    if max_deg is None:
+        max_deg = n
+    if tri_bound is None:
+        tri_bound = m * max(max_deg - 1, 0) // 3
+    grid = sms * cta_per_sm
     per_edge = nnz * (4 + 4 + 8 + 8 + 8 + 8 + 8 + 8)      # col x2, rev, T, K4, C4, offsets x2
-    lists = nnz * 4 * 12                                    # id and position lists (triangle factor)
+    lists = 36 * tri_bound
     per_vertex = n * 8 * 12
-    sweep = n * sms * ((4 + 4 + 8) * cta_per_sm + 4 * 3 + 8 * 2)
+    sweep = n * (grid * (8 + 8 + 8) + 8 * sms * 4) + max_deg * grid * (8 + 16)
     return int(per_edge + lists + per_vertex + sweep + (64 << 20))
 
 
@@ -53,14 +83,20 @@ class Request:
     t_admit: float = 0.0
     t_start: float = 0.0
     t_finish: float = 0.0
+    predicted_s: float = 0.0                          # predicted GPU seconds of its census
     device: tuple = field(default=None, repr=False)   # resident device copies (row_ptr, col)
 
 
 class CensusServer:
     def __init__(self, budget_bytes: float = 120e9, workers: int = 2, max_batch: int = 512,
-                 max_batch_edges: int = 20_000_000, run_batch=None, upload=None, device=0):
+                 max_batch_edges: int = 20_000_000, max_batch_seconds: float = 0.25, run_batch=None, upload=None,
+                 device=0, predictor: Predictor | None = None):
         self.budget = int(budget_bytes)
+        self.max_batch_seconds = max_batch_seconds
+        self.predictor = predictor or Predictor()
+        self.batch_predictions: list[tuple[float, float]] = []   # (predicted, measured) seconds per batch
         self.in_use = 0
+        self.pending_uploads = 0
         self.max_batch = max_batch
         self.max_batch_edges = max_batch_edges
         self.waiting: deque[Request] = deque()      # arrived, not admitted
@@ -82,9 +118,17 @@ class CensusServer:
         row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         col = np.ascontiguousarray(col, dtype=np.int32)
         n = len(row_ptr) - 1 if n is None else int(n)
-        m = int(row_ptr[-1]) // 2 if n > 0 else 0
         fut: Future = Future()
-        req = Request(n, row_ptr, col, fut, time.perf_counter(), footprint_bytes(n, m))
+        if n < 0 or len(row_ptr) != n + 1 or (n > 0 and (row_ptr[0] != 0 or np.any(np.diff(row_ptr) < 0)
+                                                          or row_ptr[-1] != len(col))):
+            fut.set_exception(ValueError("malformed row pointer: row_ptr[0] = 0, non-decreasing, "
+                                         "row_ptr[n] = len(col) required"))
+            return fut
+        m = int(row_ptr[-1]) // 2 if n > 0 else 0
+        deg = np.diff(row_ptr) if n > 0 else np.zeros(0, np.int64)
+        need = footprint_bytes(n, m, triangle_bound(row_ptr, col), int(deg.max()) if n > 0 else 0)
+        req = Request(n, row_ptr, col, fut, time.perf_counter(), need)
+        req.predicted_s = self.predictor.seconds(host_counts(row_ptr, col))
         if req.bytes > self.budget:
             fut.set_exception(MemoryError(f"request needs ~{req.bytes} B, budget is {self.budget} B"))
             return fut
@@ -92,8 +136,8 @@ class CensusServer:
             if self.closed:
                 raise RuntimeError("server closed")
             self.waiting.append(req)
-            self._admit_locked()
-            self.lock.notify_all()
+            reserved = self._reserve_locked()
+        self._upload_reserved(reserved)
         return fut
 
     def close(self, wait: bool = True):
@@ -105,38 +149,68 @@ class CensusServer:
                 t.join()
 
     # ------------------------------------------------------------------ internals
-    def _admit_locked(self):
-        # FIFO: the head waits until it fits, later requests do not overtake it
+    def _reserve_locked(self):
+        """Take the waiting requests that fit, FIFO (the head waits until it
+        fits, later requests do not overtake it), and reserve their bytes.
+        Their uploads happen outside the lock (_upload_reserved)."""
+        reserved = []
         while self.waiting and self.in_use + self.waiting[0].bytes <= self.budget:
             req = self.waiting.popleft()
             self.in_use += req.bytes
+            self.pending_uploads += 1
             req.t_admit = time.perf_counter()
+            reserved.append(req)
+        return reserved
+
+    def _upload_reserved(self, reserved):
+        """Copy reserved requests to the device without holding the lock, then
+        hand them to the workers (or release their bytes if the copy failed)."""
+        done = []
+        for req in reserved:
             try:
                 req.device = self._upload(req)
+                done.append((req, None))
             except Exception as e:                       # upload failed: release and report
-                self.in_use -= req.bytes
-                req.future.set_exception(e)
-                continue
-            self.admitted.append(req)
+                done.append((req, e))
+        if not done:
+            return
+        with self.lock:
+            self.pending_uploads -= len(done)
+            for req, err in done:
+                if err is None:
+                    self.admitted.append(req)
+                else:
+                    self.in_use -= req.bytes
+            more = self._reserve_locked() if any(err is not None for _, err in done) else []
+            self.lock.notify_all()
+        for req, err in done:
+            if err is not None:
+                req.future.set_exception(err)
+        self._upload_reserved(more)
+
+    def _uploading(self) -> bool:
+        """Some reserved request is still being copied to the device."""
+        return self.pending_uploads > 0
 
     def _take_batch_locked(self):
-        batch, edges = [], 0
+        batch, edges, secs = [], 0, 0.0
         while self.admitted and len(batch) < self.max_batch:
             r = self.admitted[0]
             e = int(r.row_ptr[-1]) if r.n > 0 else 0
-            if batch and edges + e > self.max_batch_edges:
+            if batch and (edges + e > self.max_batch_edges or secs + r.predicted_s > self.max_batch_seconds):
                 break
             batch.append(self.admitted.popleft())
             edges += e
+            secs += r.predicted_s
         return batch
 
     def _worker(self, k: int):
         stream = self._make_stream()
         while True:
             with self.lock:
-                while not self.admitted and not (self.closed and not self.waiting):
+                while not self.admitted and not (self.closed and not self.waiting and not self._uploading()):
                     self.lock.wait(timeout=0.05)
-                if not self.admitted and self.closed and not self.waiting:
+                if not self.admitted and self.closed and not self.waiting and not self._uploading():
                     return
                 batch = self._take_batch_locked()
             if not batch:
@@ -157,8 +231,10 @@ class CensusServer:
                     self.in_use -= r.bytes
                     self.completed.append(r)
                 self.batches.append(len(batch))
-                self._admit_locked()
+                self.batch_predictions.append((sum(r.predicted_s for r in batch), t1 - t0))
+                reserved = self._reserve_locked()
                 self.lock.notify_all()
+            self._upload_reserved(reserved)
             for i, r in enumerate(batch):
                 if err is not None:
                     r.future.set_exception(err)
@@ -204,9 +280,13 @@ class CensusServer:
         lat = np.array([r.t_finish - r.t_arrive for r in self.completed]) * 1000.0
         if lat.size == 0:
             return {}
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "count": int(lat.size),
-                "mean_batch": float(np.mean(self.batches)) if self.batches else 0.0}
+        out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "mean_ms": float(lat.mean()), "count": int(lat.size),
+               "mean_batch": float(np.mean(self.batches)) if self.batches else 0.0}
+        if self.batch_predictions:
+            rel = [abs(p / m - 1.0) for p, m in self.batch_predictions if m > 0]
+            out["predicted_vs_measured_batch_time_median_rel_err"] = float(np.median(rel)) if rel else None
+        return out
 
 
 def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:

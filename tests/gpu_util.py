@@ -29,3 +29,22 @@ def graph_hash(g) -> str:
     h.update(g.row_ptr.astype("<i8").tobytes())
     h.update(g.col.astype("<i4").tobytes())
     return h.hexdigest()
+
+
+def gpu_batch(graphs, device=False):
+    """escape_census5_batch over the block-diagonal union of `graphs`."""
+    from paper_1610_09411_gb300 import escape as esc
+    voff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    rps, cols, base = [], [], 0
+    for k, g in enumerate(graphs):
+        voff[k + 1] = voff[k] + g.n
+        rps.append(g.row_ptr[:-1] + base)
+        cols.append(g.col)
+        base += g.nnz
+    rp = np.concatenate(rps + [np.array([base])]).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    if device:
+        import torch
+        return esc.escape_census5_batch(torch.from_numpy(voff).cuda(), torch.from_numpy(rp).cuda(),
+                                        torch.from_numpy(col).cuda())
+    return esc.escape_census5_batch(voff, rp, col)

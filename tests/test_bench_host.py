@@ -22,12 +22,22 @@ def test_kernel_digest_covers_the_kernel_only(tmp_path, monkeypatch):
     # an edit outside the kernel, its counters and its launch lines: same digest
     path.write_text(text + "\n// a note at the end of the file\n")
     assert bench.source_digest("k_pairs") == base
-    # an edit inside the kernel's body: a different digest
-    sig = text.index(" k_pairs(")
+    # an edit of another sweep: same digest
+    w = text.index("k_wheels_cta(")
+    path.write_text(text[:w] + "/* other */ " + text[w:])
+    assert bench.source_digest("k_pairs") == base
+    # an edit inside a pair-sweep kernel's body: a different digest
+    sig = text.index(" k_pairs_grp(")
     body = text.index("{", sig)
     path.write_text(text[:body + 1] + "\n  // changed\n" + text[body + 1:])
     assert bench.source_digest("k_pairs") != base
     # an edit of its launch configuration: a different digest
-    path.write_text(text.replace("static constexpr int PAIR_CTAS_PER_SM = 3;", "static constexpr int PAIR_CTAS_PER_SM = 2;"))
+    old = "static constexpr int PAIR_TASK = 32 * 4 * 4;"
+    assert old in text
+    path.write_text(text.replace(old, "static constexpr int PAIR_TASK = 32 * 4 * 8;"))
+    assert bench.source_digest("k_pairs") != base
+    plan = "const size_t budget = (size_t)std::max(l2, 1 << 20) / 2;"
+    assert plan in text
+    path.write_text(text.replace(plan, plan.replace("/ 2", "/ 3")))
     assert bench.source_digest("k_pairs") != base
 

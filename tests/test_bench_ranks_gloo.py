@@ -1,6 +1,5 @@
-"""The N > 1 path of bench.py (independent replicas, one per rank) on CPU:
-world size 2 over gloo; the job time is the slowest rank's and the value
-counts every rank's edges."""
+"""The N > 1 timing of bench.py on CPU: world size 2 over gloo; the job time
+is the slowest rank's, and the ranks together count one graph per step."""
 import os
 import socket
 
@@ -26,11 +25,11 @@ def _rank_main(rank, world, port, out):
     import bench
     local_ms = 100.0 + 50.0 * rank            # rank 1 is the slow one
     total = bench.slowest_rank_ms(local_ms, world, "cpu")
-    out[rank] = (total, bench.replica_value(world, 1_000_000, total / 5))
+    out[rank] = (total, bench.job_value(1_000_000, total / 5))
     dist.destroy_process_group()
 
 
-def test_two_replicas_take_the_slowest_rank_and_sum_edges():
+def test_two_ranks_take_the_slowest_rank():
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
@@ -42,11 +41,11 @@ def test_two_replicas_take_the_slowest_rank_and_sum_edges():
         p.join(timeout=120)
         assert p.exitcode == 0
     assert out[0][0] == out[1][0] == 150.0
-    # 2 ranks x 1e6 edges every 30 ms
-    assert abs(out[0][1] - 2 * 1_000_000 / 0.030) < 1e-6
+    # one graph of 1e6 edges every 30 ms
+    assert abs(out[0][1] - 1_000_000 / 0.030) < 1e-6
 
 
 def test_single_rank_is_unchanged():
     import bench
     assert bench.slowest_rank_ms(42.0, 1, "cpu") == 42.0
-    assert bench.replica_value(1, 10, 1.0) == 10_000.0
+    assert bench.job_value(10, 1.0) == 10_000.0

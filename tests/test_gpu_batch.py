@@ -83,3 +83,17 @@ def test_batch_normalize_flag():
     res = esc.escape_census5_batch(voff, rp, col, flags=esc.ESCAPE_NORMALIZE)
     for g, r in zip(graphs, res):
         assert_same_census(r, oracle.census(g))
+
+
+def test_batch_in_chunks_matches_one_chunk(monkeypatch):
+    """A batch counted in several chunks (a small work-space budget forces
+    them) gives every graph's census, the same as one chunk and the oracle."""
+    from gpu_util import gpu_batch
+    graphs = [gg.batch_member(k, 2024, n_hi=300) for k in range(18)] + [gg.complete(30), gg.empty(2)]
+    one = gpu_batch(graphs)
+    monkeypatch.setenv("ESC_BATCH_CHUNK_MB", "4")
+    many = gpu_batch(graphs, device=True)
+    for g, a, b in zip(graphs, one, many):
+        assert_same_census(b, a)
+    for g, b in list(zip(graphs, many))[::5]:
+        assert_same_census(b, oracle.census(g))

@@ -15,7 +15,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from gpu_util import assert_same_census, gpu_census
+from gpu_util import assert_same_census, gpu_batch, gpu_census, graph_hash
 
 pytestmark = pytest.mark.gpu
 
@@ -217,13 +217,60 @@ def test_device_and_host_pointers_agree():
     assert_same_census(gpu_census(g), gpu_census(g, device=True))
 
 
-def test_rmat_scale22_full_size_sampled():
-    """R-MAT scale 22 (the benchmark workload): per-element values at sampled
-    edges/vertices against the oracle's single-element definitions, and
-    invariants of the full census."""
+def _check_stored_elements(g, pe, el):
+    """Per-element GPU values (input CSR layout) at the stored sample."""
+    verts = np.array(el["vertices"], dtype=np.int64)
+    for k in ("t_i", "C4_i", "K4_i"):
+        if k in el:
+            assert [int(x) for x in pe[k][verts]] == [int(x) for x in el[k]], k
+    slots = []
+    for u, v in el["edges"]:
+        row = g.col[g.row_ptr[u]:g.row_ptr[u + 1]]
+        q = int(np.searchsorted(row, v))
+        assert row[q] == v
+        slots.append(int(g.row_ptr[u]) + q)
+    slots = np.array(slots, dtype=np.int64)
+    for k in ("T_e", "C4_e", "K4_e"):
+        if k in el:
+            assert [int(x) for x in pe[k][slots]] == [int(x) for x in el[k]], k
+
+
+def test_rmat_scale20_full_census_matches_stored_oracle():
+    """R-MAT scale 20 (the headline generator and parameters at a quarter of
+    the size; stored oracle result of the whole census): every induced and
+    non-induced count bit for bit, and the per-element values at the sampled
+    vertices and edges (the highest-degree ones among them) when stored."""
+    path = os.path.join(GOLDEN, "census_rmat20.json")
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle result")
+    with open(path) as f:
+        gold = json.load(f)
+    g = gg.config_rmat(20, 1)
+    assert gold["sha256"] == graph_hash(g)
+    got = gpu_census(g, per_element="elements" in gold, device=True)
+    for key in ("c3", "c4", "c5", "n3", "n4", "n5"):
+        assert got[key] == [int(x) for x in gold[key]], key
+    if "elements" in gold:
+        _check_stored_elements(g, got["per_element"], gold["elements"])
+
+
+def test_rmat_scale22_full_size():
+    """R-MAT scale 22 (the benchmark workload): the full census against the
+    stored oracle result when one exists; otherwise the invariants of the
+    census, and the per-element values at the sampled vertices and edges --
+    the ten highest-degree vertices, their mutual edges and first entries among
+    them -- against the oracle's single-element definitions (stored, or
+    computed here for a sample of non-hub vertices and edges)."""
     g = gg.config_rmat()
     got = gpu_census(g, per_element=True, device=True)
     n = g.n
+    path = os.path.join(GOLDEN, "census_rmat22.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            gold = json.load(f)
+        assert gold["sha256"] == graph_hash(g)
+        for key in ("c3", "c4", "c5", "n3", "n4", "n5"):
+            assert got[key] == [int(x) for x in gold[key]], key
     assert sum(got["c5"]) == comb(n, 5) and sum(got["c4"]) == comb(n, 4) and sum(got["c3"]) == comb(n, 3)
     assert min(got["c5"] + got["c4"]) >= 0
     pe = got["per_element"]
@@ -231,6 +278,12 @@ def test_rmat_scale22_full_size_sampled():
     assert int(pe["T_e"].sum()) == 6 * T and int(pe["t_i"].sum()) == 3 * T
     assert int(pe["C4_e"].sum()) == 8 * got["n4"][3] and int(pe["C4_i"].sum()) == 4 * got["n4"][3]
     assert int(pe["K4_e"].sum()) == 12 * got["n4"][5] and int(pe["K4_i"].sum()) == 4 * got["n4"][5]
+    el_path = os.path.join(GOLDEN, "elements_rmat22.json")
+    if os.path.exists(el_path):
+        with open(el_path) as f:
+            el = json.load(f)
+        assert el["sha256"] == graph_hash(g)
+        _check_stored_elements(g, pe, el["elements"])
     rng = np.random.default_rng(2024)
     src = np.repeat(np.arange(n), g.degrees())
     idx = rng.choice(g.nnz, size=40, replace=False)
@@ -326,3 +379,50 @@ def test_batch_matches_single_graph_calls():
     for g, r in zip(graphs, res):
         assert_same_census(r, gpu_census(g))
     assert_same_census(res[0], oracle.census(graphs[0]))
+
+
+# ------------------------------------------------------------------ dense graphs (large out-degrees)
+
+def _closed(n5_idx_vals, n):
+    c = [0] * 34
+    for i, v in n5_idx_vals:
+        c[i] += v
+    return c
+
+
+@pytest.mark.parametrize("n", [1250, 1400])
+def test_complete_graph_beyond_the_shared_memory_bit_matrix(n):
+    """K_n with out-degrees above what the clique pass's shared-memory bit
+    matrix holds: every 5-subset is a 5-clique (class 21), every 4-subset a
+    4-clique, every 3-subset a triangle."""
+    got = gpu_census(gg.complete(n))
+    assert got["c5"] == _closed([(20, comb(n, 5))], n)
+    assert got["c4"][5] == comb(n, 4) and sum(got["c4"]) == comb(n, 4)
+    assert got["c3"] == [0, 0, 0, comb(n, 3)]
+
+
+def test_complete_bipartite_beyond_the_shared_memory_bit_matrix():
+    """K_{a,b}, a = b = 1300: a 5-subset with k vertices on one side is empty
+    (k = 0, 5), a 4-star (k = 1, 4) or K_{2,3} (k = 2, 3)."""
+    a = b = 1300
+    got = gpu_census(gg.complete_bipartite(a, b))
+    want = _closed([(21, comb(a, 5) + comb(b, 5)), (0, a * comb(b, 4) + b * comb(a, 4)),
+                    (12, comb(a, 2) * comb(b, 3) + comb(a, 3) * comb(b, 2))], a + b)
+    assert got["c5"] == want
+
+
+def test_dense_batch_member_matches_stored_oracle():
+    """Member 24 of the batch workload, G(1250, 0.279) (stored oracle result)."""
+    gold_path = os.path.join(GOLDEN, "census_batch24.json")
+    if not os.path.exists(gold_path):
+        pytest.skip("no stored oracle result")
+    with open(gold_path) as f:
+        gold = json.load(f)
+    g = gg.batch_member(24, 2024)
+    assert gold["sha256"] == graph_hash(g)
+    got = gpu_census(g)
+    for key in ("c3", "c4", "c5", "n3", "n4", "n5"):
+        assert got[key] == [int(x) for x in gold[key]], key
+    res = gpu_batch([g, gg.batch_member(25, 2024), gg.batch_member(26, 2024)])
+    for key in ("c3", "c4", "c5", "n3", "n4", "n5"):
+        assert res[0][key] == [int(x) for x in gold[key]], key

@@ -855,14 +855,19 @@ static constexpr int64_t PH_LARGE_W = PH_LARGE_SLOTS / 2;
 
 // w_i of every vertex with degree >= 2, appended to the list of its class
 // (roughly by decreasing rank, so the heaviest items come first)
-__global__ void k_pair_classify(DevGraph g, int32_t* lists, unsigned long long* cnts, long long w_small,
-                                long long w_large, Owner own) {
+// Also the largest common-neighbour list (triangles on one edge) into cnts[7].
+__global__ void k_pair_classify(DevGraph g, const uint32_t* T, int32_t* lists, unsigned long long* cnts,
+                                long long w_small, long long w_large, Owner own) {
   int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t k = warp; k < g.n; k += nwarps) {
     int64_t i = g.n - 1 - k;
     int64_t b0 = g.R[i], e0 = g.R[i + 1];
+    unsigned tmax = 0;
+    for (int64_t p = b0 + lane; p < e0; p += 32) tmax = max(tmax, T[p]);
+    tmax = __reduce_max_sync(0xffffffffu, tmax);
+    if (lane == 0 && tmax) atomicMax(&cnts[7], (unsigned long long)tmax);
     if (e0 - b0 < 2 || !own.owns(i)) continue;
     unsigned long long w = 0;
     for (int64_t p = b0 + lane; p < e0; p += 32) w += (unsigned long long)(g.rev[p] - g.R[g.C[p]]);
@@ -1336,9 +1341,11 @@ static constexpr int WHEEL_CHUNK = 64;
 // (counts there can pass 2^16); before each increment an atomicMax with the
 // current tag turns an older entry into a zero count, so no clearing pass
 // walks the lists a second time.  A CTA's tags grow with the u's it takes.
+// win16: every count of the sweep stays below 2^16 (the largest common-
+// neighbour list is shorter), so large centres keep a shared-memory window.
 __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, int64_t nitems,
                              unsigned long long* qctr, TriLists tl3, const uint32_t* T, unsigned long long* gscr,
-                             int64_t gscr_stride, int smem_cap, AccSet acc) {
+                             int64_t gscr_stride, int smem_cap, AccSet acc, bool win16) {
   extern __shared__ uint32_t sscr[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
@@ -1381,10 +1388,21 @@ __global__ void k_wheels_cta(DevGraph g, int64_t c0, const int64_t* item_off, in
           part += atomicAdd(&sscr[pv], 1u) & 0xffffu;
         });
       } else {
+        // a centre too large for shared memory: its last smem_cap positions
+        // (the highest ranks, where the common neighbours concentrate) stay
+        // there when every count fits 16 bits (win16), the rest in global memory
         const unsigned long long t32 = (unsigned long long)tag << 32;
+        const uint32_t t16 = tag << 16;
+        const int wstart = win16 ? d - smem_cap : d;
         wheel_links(tl3, T, base, Lu, lenu, pu, (uint32_t)wid, (uint32_t)nw, [&](int32_t pv) {
-          atomicMax(&g64[pv], t32);
-          part += (uint32_t)atomicAdd(&g64[pv], 1ull);
+          if (pv >= wstart) {
+            uint32_t* c = &sscr[pv - wstart];
+            atomicMax(c, t16);
+            part += atomicAdd(c, 1u) & 0xffffu;
+          } else {
+            atomicMax(&g64[pv], t32);
+            part += (uint32_t)atomicAdd(&g64[pv], 1ull);
+          }
         });
       }
       la.v[0] += part;
@@ -2344,7 +2362,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     // (ESC_PAIR_SMALL_W / ESC_PAIR_LARGE_W lower them for tuning)
     const long long w_small = std::min<long long>(PH_SMALL_W, env_int("ESC_PAIR_SMALL_W", PH_SMALL_W + 1) - 1);
     const long long w_large = std::min<long long>(PH_LARGE_W, env_int("ESC_PAIR_LARGE_W", PH_LARGE_W + 1) - 1);
-    (k_pair_classify<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, b_plist.as<int32_t>(),
+    (k_pair_classify<<<grid_for(n * 32, TPB, sms), TPB, 0, s>>>(g, T, b_plist.as<int32_t>(),
                                                                 b_pctr.as<unsigned long long>(), w_small,
                                                                 std::max(w_small, w_large), own), note_launch());
     cudaMemcpyAsync(pcnt, b_pctr.p, sizeof(pcnt), cudaMemcpyDeviceToHost, s);
@@ -2473,7 +2491,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   mark(6, 0, s3);
   if (five && c0 < n)
     (k_wheels_cta<<<2 * sms, 512, smem_w, s3>>>(g, c0, b_io.as<int64_t>(), nitems_w, ctr + 5, tl3, T,
-                                            b_gs.as<unsigned long long>(), gstride, smem_cap, accs), note_launch());
+                                            b_gs.as<unsigned long long>(), gstride, smem_cap, accs,
+                                            pcnt[7] < 65536 && env_int("ESC_WHEEL_WINDOW", 2) != 1), note_launch());
   if (five && c0 > 0) {
     int per_sm = 1;
     ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wheels_warp, 256, 0));

@@ -91,6 +91,8 @@ def _load(parallel: bool = False):
         lib.oracle_edge_elements.argtypes = [i64, P, P, i64, P, P, P, P, P]
         lib.oracle_vertex_elements.restype = c_int
         lib.oracle_vertex_elements.argtypes = [i64, P, P, i64, P, P, P]
+        lib.oracle_wedge_diamond_sums.restype = c_int
+        lib.oracle_wedge_diamond_sums.argtypes = [i64, P, P, P]
         lib.oracle_num_sums.restype = c_int
         lib.oracle_num_threads.restype = c_int
         assert lib.oracle_num_sums() == len(SUM_NAMES)
@@ -269,6 +271,18 @@ def census(g, per_element: bool = False, parallel: bool = False) -> dict:
     if arrs is not None:
         out["per_element"] = arrs
     return out
+
+
+def wedge_diamond_sums(g, parallel: bool = False) -> dict:
+    """W (wedges), T (triangles) and D (diamonds, sum over edges of C(T(e), 2))
+    from their definitions, without the rest of the census."""
+    rp, col = _csr(g)
+    out = np.zeros(6, dtype=np.uint64)
+    rc = _load(parallel).oracle_wedge_diamond_sums(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data)
+    if rc:
+        raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
+    vals = [int(out[2 * k]) | (int(out[2 * k + 1]) << 64) for k in range(3)]
+    return dict(zip(("W", "T", "D"), vals))
 
 
 def edge_elements(g, us, vs) -> dict:

@@ -855,6 +855,42 @@ static int64_t* two_hop(int64_t n, const int64_t* rp, const int32_t* col, int64_
   return touched;
 }
 
+/* ------------------------------------------------------------------ */
+/* Wedges, triangles and diamonds alone (the unit counts of the census's */
+/* algorithmic-byte model, for graphs whose full census is out of reach): */
+/*   W = sum_i C(d(i), 2), T = (1/3) sum over edges of T(e),             */
+/*   D = sum over edges e of C(T(e), 2), T(e) = |N(u) cap N(v)| by merge. */
+/* out: 3 entries of two u64 words (lo, hi): W, T, D.                    */
+/* ------------------------------------------------------------------ */
+int oracle_wedge_diamond_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_t* out) {
+  int rc = validate(n, rp, col);
+  if (rc) return rc;
+  g_ovf = 0;
+  u128 W = 0, T3 = 0, D = 0;
+  for (int64_t u = 0; u < n; ++u) W = add(W, ch2((uint64_t)(rp[u + 1] - rp[u])));
+  const int nw = oracle_num_threads();
+  u128* part = (u128*)calloc((size_t)nw * 2, sizeof(u128));
+  if (!part) return ORACLE_ENOMEM;
+#pragma omp parallel
+  {
+    u128* mine = part + 2 * thread_id();
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t u = 0; u < n; ++u)
+      for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+        int64_t v = col[p];
+        if (v <= u) continue;                   /* each edge once */
+        uint64_t te = (uint64_t)merge_count(col + rp[u], rp[u + 1] - rp[u], col + rp[v], rp[v + 1] - rp[v]);
+        mine[0] = add(mine[0], te);
+        mine[1] = add(mine[1], ch2(te));
+      }
+  }
+  for (int t = 0; t < nw; ++t) { T3 = add(T3, part[2 * t]); D = add(D, part[2 * t + 1]); }
+  free(part);
+  u128 vals[3] = {W, T3 / 3, D};
+  for (int k = 0; k < 3; ++k) { out[2 * k] = (uint64_t)vals[k]; out[2 * k + 1] = (uint64_t)(vals[k] >> 64); }
+  return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
+}
+
 int oracle_edge_elements(int64_t n, const int64_t* rp, const int32_t* col, int64_t count,
                          const int64_t* us, const int64_t* vs, uint64_t* T, uint64_t* K4, uint64_t* C4) {
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));

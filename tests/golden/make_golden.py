@@ -8,6 +8,7 @@ computed for (and recompute them live if not).
     python tests/golden/make_golden.py chung_lu er500 two_hubs
     python tests/golden/make_golden.py --parallel rmat20 batch24
     python tests/golden/make_golden.py --elements rmat22
+    python tests/golden/make_golden.py --parallel --sums rmat22
 
 --parallel runs the OpenMP build of the same oracle source on OMP_NUM_THREADS
 threads (its equality with the serial build is pinned in test_oracle_pins).
@@ -112,11 +113,28 @@ def write_elements(name):
     print(name, "elements", out["oracle_seconds"], "s")
 
 
+def write_sums(name, parallel=False):
+    """W, T and D of a workload from their definitions (oracle.wedge_diamond_sums):
+    the unit counts of the benchmark's byte model where the full census is out of reach."""
+    g = WORKLOADS[name]()
+    t0 = time.time()
+    w = oracle.wedge_diamond_sums(g, parallel=parallel)
+    out = {"workload": name, "graph": g.name, "n": g.n, "m": g.m, "sha256": graph_hash(g),
+           "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": oracle.num_threads(parallel),
+           "oracle_host": f"{platform.machine()}, {os.cpu_count()} cores",
+           "sums": {k: str(v) for k, v in w.items()}}
+    with open(os.path.join(HERE, f"sums_{name}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, "sums", out["oracle_seconds"], "s")
+
+
 if __name__ == "__main__":
     par = "--parallel" in sys.argv
     names = [a for a in sys.argv[1:] if not a.startswith("--")]
     for name in names or ["chung_lu", "er500", "two_hubs"]:
         if "--elements" in sys.argv:
             write_elements(name)
+        elif "--sums" in sys.argv:
+            write_sums(name, par)
         else:
             write(name, par)

@@ -283,3 +283,19 @@ def test_parallel_build_equals_brute_force_and_serial():
             assert np.array_equal(par["per_element"][k], ser["per_element"][k]), (g.name, k)
         if g.n <= 40:
             assert par["c5"] == oracle.brute_census(g)["c5"], g.name
+
+
+def test_wedge_diamond_sums_equal_the_census_sums():
+    """W, T and D alone (the unit counts of the byte model for the largest
+    workload) agree with the full census's sums and with brute force."""
+    for g in _graphs_small() + [gg.chung_lu(3000, 2.1, 8, 300, 5)]:
+        s = oracle.census(g)["sums"]
+        for par in (False, True):
+            w = oracle.wedge_diamond_sums(g, parallel=par)
+            assert w == {"W": s["W"], "T": s["T"], "D": s["D"]}, g.name
+        if g.n <= 40:
+            b = oracle.brute_census(g)
+            # 3-vertex wedges (induced) + 3 x triangles = W; 4-vertex induced diamonds + 6 x K4 = D
+            assert w["W"] == b["c3"][2] + 3 * b["c3"][3]
+            assert w["T"] == b["c3"][3]
+            assert w["D"] == b["c4"][4] + 6 * b["c4"][5]

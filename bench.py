@@ -71,20 +71,23 @@ def make_graph(name: str):
 
 def oracle_sums(name: str, g):
     """Counts the algorithmic-byte formulas need, as stored by the oracle
-    (tests/golden); None when no stored result matches this graph."""
+    (tests/golden: the whole census's sums, or W, T and D alone); None when no
+    stored result matches this graph."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     try:
         from gpu_util import graph_hash
-        path = os.path.join(ROOT, "tests", "golden", f"census_{name}.json")
-        if not os.path.exists(path):
-            return None
-        with open(path) as f:
-            gold = json.load(f)
-        if gold["sha256"] != graph_hash(g):
-            return None
-        return {k: int(v) for k, v in gold["sums"].items()}
+        for kind in ("census", "sums"):
+            path = os.path.join(ROOT, "tests", "golden", f"{kind}_{name}.json")
+            if not os.path.exists(path):
+                continue
+            with open(path) as f:
+                gold = json.load(f)
+            if gold["sha256"] != graph_hash(g):
+                continue
+            return {k: int(v) for k, v in gold["sums"].items()}
     except Exception:
-        return None
+        pass
+    return None
 
 
 def measured_peak():

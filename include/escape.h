@@ -262,6 +262,17 @@ void escape_free(escape_graph* g);
 /* Static string for a status code. */
 const char* escape_status_str(escape_status s);
 
+/*
+ * escape_last_cuda_error -- the CUDA runtime error (a cudaError_t value) of
+ * the last failing CUDA call that a call of this library turned into a status
+ * on the calling thread (always for ESCAPE_ECUDA; ESCAPE_ENOMEM and
+ * ESCAPE_EOVERFLOW can also come from host-side checks, which leave it
+ * unchanged), or 0 if there has been none.  If name is not NULL, *name
+ * receives the error's symbolic name (static storage owned by the CUDA
+ * runtime; "" for 0).  Diagnostic only: the value is per host thread.
+ */
+int escape_last_cuda_error(const char** name);
+
 #ifdef __cplusplus
 }
 #endif

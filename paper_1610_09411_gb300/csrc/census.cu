@@ -2094,8 +2094,7 @@ static cudaError_t plan_pair_clusters(bool big, int sms, size_t arr_bytes, int64
     int64_t want = std::max<int64_t>(0, (jbig - n0 + 1) / 2);        // words covering every countable rank
     plan->win_words = (int)std::max<int64_t>(0, std::min<int64_t>(bytes / 4, want));
     plan->wlo = std::max<int64_t>(n0, jbig - 2 * (int64_t)plan->win_words);
-    if (plan->win_words > 0)
-      ESC_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->win_words * 4));
+    if (plan->win_words > 0) ESC_TRY(allow_max_smem(k, smem_optin));   // the limit is the same for every graph
   }
   int per_sm = 1;
   ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan->threads, plan->win_words * 4));

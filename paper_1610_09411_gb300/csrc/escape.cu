@@ -27,10 +27,18 @@ struct escape_graph {
   bool has_part = false;      // a part of a split census is held (pe, ori)
 };
 
+namespace esc {
+static thread_local int t_last_cuda = 0;   // escape_last_cuda_error
+void note_cuda_error(cudaError_t e) {
+  if (e != cudaSuccess) t_last_cuda = (int)e;
+}
+}  // namespace esc
+
 namespace {
 
 escape_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return ESCAPE_OK;
+  esc::note_cuda_error(e);
   if (e == cudaErrorMemoryAllocation) return ESCAPE_ENOMEM;
   if (e == cudaErrorInvalidConfiguration) return ESCAPE_EOVERFLOW;
   cudaGetLastError();   // clear a non-sticky error
@@ -316,6 +324,12 @@ escape_status census_one(escape_graph* g, const int64_t* d_rp, const int32_t* d_
 }  // namespace
 
 extern "C" {
+
+int escape_last_cuda_error(const char** name) {
+  const int e = esc::t_last_cuda;
+  if (name) *name = e ? cudaGetErrorName((cudaError_t)e) : "";
+  return e;
+}
 
 const char* escape_status_str(escape_status s) {
   switch (s) {

@@ -37,6 +37,8 @@ struct Oriented {
 
 // Counts kernel launches made by this thread (reported per census call).
 void note_launch();
+// Records a failing CUDA call of the calling thread (escape_last_cuda_error).
+void note_cuda_error(cudaError_t e);
 long long launches_so_far();
 
 int bits_for(int64_t n);

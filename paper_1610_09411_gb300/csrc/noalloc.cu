@@ -129,13 +129,16 @@ extern "C" escape_status escape_cycles4_noalloc(int64_t n, const int64_t* row_pt
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) return ESCAPE_ECUDA;
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    esc::note_cuda_error(e);
+    return ESCAPE_ECUDA;
+  }
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
       e = cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch);
-      if (e != cudaSuccess) { g_addr[dev] = nullptr; cudaGetLastError(); return ESCAPE_ECUDA; }
+      if (e != cudaSuccess) { g_addr[dev] = nullptr; cudaGetLastError(); esc::note_cuda_error(e); return ESCAPE_ECUDA; }
     }
     base = g_addr[dev];
   }
@@ -144,7 +147,7 @@ extern "C" escape_status escape_cycles4_noalloc(int64_t n, const int64_t* row_pt
   e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int) * (size_t)NA_WORDS, s);
   if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(c4_v, 0, sizeof(uint64_t) * (size_t)n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c4_total, 0, sizeof(uint64_t), s);
-  if (e != cudaSuccess) { cudaGetLastError(); return ESCAPE_ECUDA; }
+  if (e != cudaSuccess) { cudaGetLastError(); esc::note_cuda_error(e); return ESCAPE_ECUDA; }
   if (n > 0) {
     k_cycles4_noalloc<<<NA_CTAS, NA_THREADS, 0, s>>>(row_ptr, col, n, scratch, (unsigned long long*)c4_v,
                                                      (unsigned long long*)c4_total);
@@ -155,6 +158,6 @@ extern "C" escape_status escape_cycles4_noalloc(int64_t n, const int64_t* row_pt
     e = cudaMemcpyAsync(&status, scratch + (int64_t)NA_CTAS * NA_MAX_N * 2 + 2, sizeof(unsigned int),
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { cudaGetLastError(); return ESCAPE_ECUDA; }
+  if (e != cudaSuccess) { cudaGetLastError(); esc::note_cuda_error(e); return ESCAPE_ECUDA; }
   return status ? ESCAPE_EINVAL : ESCAPE_OK;
 }

@@ -97,6 +97,8 @@ def _load():
     lib.escape_free.argtypes = [P]
     lib.escape_status_str.restype = ctypes.c_char_p
     lib.escape_status_str.argtypes = [c_int]
+    lib.escape_last_cuda_error.restype = c_int
+    lib.escape_last_cuda_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
     return lib
 
 
@@ -115,8 +117,20 @@ def _stream(stream):
     return None
 
 
+def escape_last_cuda_error():
+    """(code, name) of the last CUDA error the library turned into a status
+    on this thread; (0, "") if none."""
+    name = ctypes.c_char_p()
+    code = LIB.escape_last_cuda_error(ctypes.byref(name))
+    return code, (name.value or b"").decode()
+
+
 def _check(code: int, what: str):
     if code != 0:
+        if code == 3:                  # ECUDA: name the CUDA error behind it
+            cu, name = escape_last_cuda_error()
+            if cu:
+                what = f"{what} [{name} ({cu})]"
         raise EscapeError(code, what)
 
 

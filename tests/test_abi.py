@@ -34,6 +34,7 @@ def test_binding_loads_and_has_every_entry_point():
         assert hasattr(esc, name), f"binding lacks {name}"
     assert esc.escape_status_str(0) == "ok"
     assert "invalid" in esc.escape_status_str(1)
+    assert esc.escape_last_cuda_error() == (0, "")      # no CUDA call has failed on this thread
 
 
 def test_sources_target_sm103a_only():

@@ -159,3 +159,45 @@ def test_gpu_results_alone_and_in_the_mix_equal_the_oracle():
         for k in ("c3", "c4", "c5", "n3", "n4", "n5"):
             assert b[k] == w[k]          # served result = the oracle's
             assert a[k] == w[k]          # the census alone = the oracle's
+
+
+@pytest.mark.gpu
+def test_concurrent_censuses_with_heavy_pair_items_equal_the_oracle():
+    """Censuses on three host threads at once, each on its own stream, over
+    graphs whose heavy pair items use shared-memory windows of different
+    widths (the launch limits one thread sets must hold for the others'
+    launches); every result equals the oracle's."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1610_09411_gb300 import build
+    build.build()
+    from paper_1610_09411_gb300 import escape as esc
+    import oracle
+    graphs = [gg.chung_lu(20000, 2.1, 10, 2000, 8), gg.chung_lu(6000, 2.1, 12, 1500, 3), gg.config_rmat(13, 2),
+              gg.chung_lu(2500, 2.1, 14, 1200, 5)]
+    want = [oracle.census(g) for g in graphs]
+    errors, done = [], []
+
+    def worker(t):
+        try:
+            torch.cuda.set_device(0)
+            st = torch.cuda.Stream()
+            for rep in range(3):
+                for k in range(len(graphs)):
+                    idx = (k + t + rep) % len(graphs)
+                    g = graphs[idx]
+                    got = esc.census(g.row_ptr, g.col, n=g.n, stream=st.cuda_stream)
+                    for key in ("c3", "c4", "c5", "n3", "n4", "n5"):
+                        assert got[key] == want[idx][key], (t, rep, idx, key)
+                    done.append(idx)
+        except Exception as e:            # reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(3)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=600)
+    assert not errors, errors[0]
+    assert len(done) == 3 * 3 * len(graphs)

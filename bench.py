@@ -163,7 +163,7 @@ class ClockSampler:
 DIGEST_SECTIONS = {
     "k_pairs": ([("// Thm 11/12: N13", "// Thm 11: N18 (wheels)"),
                  ("struct PairPlan {", "\ncudaError_t run_census(")],
-                ("PAIR_", "PairPlan", "pplan", "plan_pair", "launch_pairs", "k_pairs", "ptasks", "tsB")),
+                ("PAIR_", "PairPlan", "pplan", "plan_pair", "launch_pairs", "k_pairs", "ptasks", "tsB", "pwin")),
 }
 
 

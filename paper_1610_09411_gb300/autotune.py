@@ -3,8 +3,9 @@
 The knobs are environment variables the library reads when it plans a census
 (results never depend on them, only the time does):
 
-  ESC_PAIR_WINDOW     1 turns off the shared-memory window of top-rank counters
-                      of the heavy pair-sweep items (2: on, the default)
+  ESC_PAIR_WINDOW     heavy pair-sweep items: 3 (the default) count every rank in
+                      successive shared-memory windows; 2 one window over the top
+                      ranks, tagged global counters below it; 1 no window
   ESC_PAIR_CLUSTER    CTAs per cluster for the heavy pair-sweep items (1, 2, 4, 8, 16;
                       the window needs 1)
   ESC_PAIR_SHAPE      heavy pair kernel: 1 = 512 threads x 3 CTAs per SM,
@@ -37,7 +38,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_PATH = os.path.join(HERE, "tuning.json")
 
 KNOBS = {
-    "ESC_PAIR_WINDOW": [2, 1],
+    "ESC_PAIR_WINDOW": [3, 2, 1],
     "ESC_PAIR_CLUSTER": [1, 2, 4, 8],
     "ESC_PAIR_SHAPE": [3, 2, 1],
     "ESC_WHEEL_WARP_MAX": [1024, 512, 256],

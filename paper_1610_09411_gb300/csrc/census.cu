@@ -1232,6 +1232,222 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pairs_grp(DevGraph g, const i
   final_flush(la, ids, acc, sh);
 }
 
+// ---------------------------------------------------------------- windowed heavy items
+// Heavy items, default form: one 1024-thread CTA per SM and item.  The ranks
+// below jbig are cut into windows of S = 2 * win_words ranks on a grid
+// anchored at jbig (window k = [jbig - (k+1) S, jbig - k S)).  An item i
+// counts its wedges window by window, from the lowest window that can hold a
+// neighbour of a neighbour up to the one holding rank min(i, jbig) - 1, every
+// increment a 16-bit shared-memory atomic.  For every c in N(i) a cursor marks
+// how far N(c) has been walked; a window takes the entries below its upper
+// end.  A finished window below the top one is written whole to the CTA's
+// dense 16-bit array; the top window stays in shared memory.  Ranks from jbig
+// on (degree >= 2^16, so counts may need more than 16 bits) go to tagged
+// 64-bit counters.  The diamond pass then reads W(i,j) from shared memory
+// (the top window, where most diamond tips lie), the dense array or the 64-bit
+// counters.
+// A count below jbig is at most d_j < 2^16.  The dense array needs no clearing:
+// a window is written whole, and the diamond pass reads only windows this item
+// wrote (a diamond tip j shares two neighbours with i, so W(i,j) >= 2 and its
+// window took increments).
+struct PairWin {
+  uint32_t* g16;              // per CTA: rank j at bits 16 ((j + par) & 1) of word (j + par) >> 1, par = jbig & 1
+  int64_t g16_words;          // (n + 2) / 2
+  longlong2* curs;            // per CTA: (cursor, end) of the list N(c) of every c in N(i)
+  int64_t curs_cap;           // >= the largest degree
+  unsigned long long* side;   // per CTA: n - jbig counters (tag << 32) | count
+  int64_t jbig, n, n0;        // n0: the first rank of degree >= 1
+  int win_words;
+};
+
+// First position q in [a, b) with C[q] >= key (C ascending there), or b; one
+// warp, 32 probes per round.
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t* C, int64_t a, int64_t b, int32_t key) {
+  const int lane = threadIdx.x & 31;
+  // C[q] < key for q < a, C[q] >= key for q >= b
+  while (b - a > 32) {
+    const int64_t step = (b - a + 31) / 32;
+    const int64_t q = a + (int64_t)lane * step;
+    const unsigned m = __ballot_sync(0xffffffffu, q >= b || C[q] >= key);
+    if (m == 0) {
+      a += 31 * step + 1;
+    } else {
+      const int f = __ffs(m) - 1;
+      b = min(b, a + (int64_t)f * step);
+      if (f > 0) a += (int64_t)(f - 1) * step + 1;
+    }
+  }
+  const int64_t q = a + lane;
+  const unsigned m = __ballot_sync(0xffffffffu, q >= b || C[q] >= key);
+  return m ? min(b, a + (int64_t)(__ffs(m) - 1)) : b;
+}
+
+// Pass 1 of one window: for every c in N(i) (this warp's share), the entries
+// of N(c) from its cursor that lie below `hi` (all remaining ones when `last`).
+// `first`: the cursors start at the heads of the lists; unless `last`, the new
+// cursors are stored.
+template <class Inc, class Defer>
+__device__ __forceinline__ u128 pair_wedges_win(const DevGraph& g, longlong2* curs, int64_t b0, int64_t e0,
+                                                int64_t gw, int64_t gnw, bool first, bool last, int32_t hi,
+                                                Inc&& inc, Defer&& defer) {
+  const int lane = threadIdx.x & 31;
+  u128 n13 = 0;
+  for (int64_t pbase = b0 + gw; pbase < e0; pbase += gnw * 32) {
+    const int64_t p = pbase + (int64_t)lane * gnw;
+    int64_t cb_l = 0, ce_l = 0;
+    if (p < e0) {
+      if (first) {
+        cb_l = g.R[g.C[p]];
+        ce_l = g.rev[p];                        // N(c) below i ends at the slot of i
+      } else {
+        const longlong2 cu = curs[p - b0];
+        cb_l = cu.x;
+        ce_l = cu.y;
+      }
+    }
+    int64_t cn_l = ce_l;                        // the lane's new cursor
+    if (ce_l - cb_l <= PAIR_SHORT) {            // short: each lane walks its own list up to hi
+      int64_t q = cb_l;
+      while (q < ce_l) {
+        int32_t jj[4];
+        uint32_t oo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jj[u] = q + u < ce_l ? __ldcs(&g.C[q + u]) : 0x7fffffff;
+        int stop = 4;
+#pragma unroll
+        for (int u = 3; u >= 0; --u)
+          if (jj[u] >= hi) stop = u;            // ascending: the first entry at or above hi
+#pragma unroll
+        for (int u = 0; u < 4; ++u) oo[u] = u < stop ? inc(jj[u]) : 1u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;
+        if (stop < 4) {
+          q += stop;
+          break;
+        }
+        q += 4;
+      }
+      cn_l = min(q, ce_l);
+    }
+    unsigned longm = __ballot_sync(0xffffffffu, ce_l - cb_l > PAIR_SHORT);
+    while (longm) {                             // long: the warp takes them one at a time
+      const int k = __ffs(longm) - 1;
+      longm &= longm - 1;
+      const int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
+      const int64_t qe = last ? ce : warp_lower_bound(g.C, cb, ce, hi);
+      if (lane == k) cn_l = qe;
+      if (qe - cb > PAIR_TASK && defer(cb, qe)) continue;
+      n13 += pair_range(g, cb, qe, inc);
+    }
+    if (!last && p < e0) curs[p - b0] = make_longlong2(cn_l, ce_l);
+  }
+  return n13;
+}
+
+template <bool BIG>
+__global__ void __launch_bounds__(1024, 1) k_pairs_win(DevGraph g, const int32_t* items, int64_t nitems,
+                                                        unsigned long long* qctr, PairWin pw, TriLists tl3,
+                                                        const uint32_t* T, AccSet acc, PairTasks pt,
+                                                        unsigned* status) {
+  extern __shared__ uint32_t win[];
+  __shared__ u128 sh[32];
+  __shared__ int64_t sh_item;
+  __shared__ int sh_flag[2];                   // a window took increments (windows alternate)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t grp = blockIdx.x;
+  const int64_t S = 2 * (int64_t)pw.win_words;
+  const int64_t par = pw.jbig & 1;
+  uint32_t* g16 = pw.g16 + grp * pw.g16_words;
+  longlong2* curs = pw.curs + grp * pw.curs_cap;
+  unsigned long long* side = pw.side + grp * (pw.n - pw.jbig);
+  uint32_t tag = 0;
+  const int ids[2] = {ACC_N13, ACC_N17};
+  LocalAcc<2> la;
+  la.zero();
+  for (int t = threadIdx.x; t < pw.win_words; t += blockDim.x) win[t] = 0u;
+  if (threadIdx.x == 0) sh_flag[0] = sh_flag[1] = 0;
+  while (true) {
+    const int64_t it = next_item(qctr, nitems, &sh_item);   // its barriers publish the cleared window
+    if (it < 0) break;
+    const int64_t i = items[it];
+    const int64_t b0 = g.R[i], e0 = g.R[i + 1];
+    if (e0 - b0 > pw.curs_cap) {                // never: sized by the largest degree
+      if (threadIdx.x == 0) set_err(status, DEVERR_SCRATCH);
+      continue;
+    }
+    if (BIG && ++tag == 0xffffffffu) {          // tags used up: zero the 64-bit counters
+      for (int64_t t = threadIdx.x; t < pw.n - pw.jbig; t += blockDim.x) side[t] = 0ull;
+      tag = 1;
+      __syncthreads();
+    }
+    const int64_t top = min(i, pw.jbig);        // ranks [0, top) are counted in windows
+    const int64_t ktop = (pw.jbig - top) / S;   // the window of rank top - 1
+    const int64_t kbot = max(ktop, (pw.jbig - 1 - pw.n0) / S);   // the window of rank n0
+    u128 n13 = 0;
+    bool top_touched = false;
+    for (int64_t k = kbot; k >= ktop; --k) {
+      const int64_t lo = pw.jbig - (k + 1) * S;
+      const bool last = k == ktop;
+      const int32_t hi = last ? 0x7fffffff : (int32_t)(pw.jbig - k * S);
+      bool tch = false;
+      auto inc = [&](int32_t j) -> uint32_t {
+        tch = true;
+        if (BIG && j >= pw.jbig) {
+          unsigned long long* q = &side[j - pw.jbig];
+          atomicMax(q, (unsigned long long)tag << 32);
+          return (uint32_t)atomicAdd(q, 1ull);
+        }
+        const int64_t q = j - lo;
+        const unsigned s16 = 16u * (unsigned)(q & 1);
+        return (atomicAdd(&win[q >> 1], 1u << s16) >> s16) & 0xffffu;
+      };
+      n13 += pair_wedges_win(g, curs, b0, e0, wid, nw, k == kbot, last, hi, inc,
+                             [&](int64_t cb, int64_t ce) { return pair_defer(pt, grp, cb, ce); });
+      __syncthreads();                          // the window's long lists are appended as tasks
+      const unsigned long long nt = __ldcg(&pt.n[grp]);
+      n13 += pair_run_tasks(g, pt, grp, nt, wid, nw, inc);
+      if (__any_sync(0xffffffffu, tch) && lane == 0) sh_flag[k & 1] = 1;
+      __syncthreads();                          // the window's counts are complete; every thread has read nt
+      const bool touched = sh_flag[k & 1] != 0;
+      if (threadIdx.x == 0) {
+        pt.n[grp] = 0;                          // the next window appends after a later barrier
+        sh_flag[(k - 1) & 1] = 0;               // the next window's flag (last read before the first barrier above)
+      }
+      if (last) {
+        top_touched = touched;
+      } else {
+        if (touched) {                          // write the window whole, then clear it
+          const int64_t w0 = (lo + par) >> 1;   // lo + par is even
+          for (int64_t t = threadIdx.x; t < pw.win_words; t += blockDim.x)
+            if (w0 + t >= 0) g16[w0 + t] = win[t];
+          __syncthreads();
+          for (int t = threadIdx.x; t < pw.win_words; t += blockDim.x) win[t] = 0u;
+        }
+        __syncthreads();
+      }
+    }
+    const int64_t lo_top = pw.jbig - (ktop + 1) * S;
+    u128 n17 = pair_diamonds(g, tl3, T, i, b0, e0, wid, nw, [&](int32_t j) -> uint32_t {
+      if (BIG && j >= pw.jbig) {
+        const unsigned long long v = __ldcg(&side[j - pw.jbig]);
+        return (uint32_t)(v >> 32) == tag ? (uint32_t)v : 0u;
+      }
+      const int64_t q = j - lo_top;
+      if (q >= 0) return (win[q >> 1] >> (16u * (unsigned)(q & 1))) & 0xffffu;
+      const int64_t t = j + par;
+      return (__ldcg(&g16[t >> 1]) >> (16u * (unsigned)(t & 1))) & 0xffffu;
+    });
+    la.v[0] += n13;
+    la.v[1] += n17;
+    __syncthreads();                            // the diamond reads of the window are done
+    if (top_touched)
+      for (int t = threadIdx.x; t < pw.win_words; t += blockDim.x) win[t] = 0u;
+    if (threadIdx.x == 0) sh_flag[0] = sh_flag[1] = 0;
+    block_item_flush(la, ids, acc, i, sh);
+  }
+  final_flush(la, ids, acc, sh);
+}
+
 // ============================================================================
 // Thm 11: N18 (wheels) = sum over centres c of the 4-cycles of G[N(c)],
 // counted by the 4-cycle rule inside the neighbourhood: for u in N(c) and
@@ -2049,6 +2265,7 @@ struct PairPlan {
   int shape = 1;                               // kernel instance, see ESC_PAIR_SHAPES
   int win_words = 0;                           // shared-memory window (clusters of one CTA)
   int64_t wlo = 0;                             // its first rank
+  bool windowed = false;                       // k_pairs_win: every rank below jbig in successive windows
 };
 
 static int env_int(const char* name, int dflt) {
@@ -2068,11 +2285,41 @@ static const void* pairs_grp_fn(bool big, int shape) {
   return nullptr;
 }
 
+// The windowed form (k_pairs_win, the default): one 1024-thread CTA per SM,
+// the window as wide as shared memory allows, but no wider than the ranks
+// [n0, jbig) need.
+static cudaError_t plan_pair_windows(bool big, int sms, int64_t n0, int64_t jbig, int smem_optin, PairPlan* plan) {
+  const void* k = big ? (const void*)k_pairs_win<true> : (const void*)k_pairs_win<false>;
+  cudaFuncAttributes fa;
+  ESC_TRY(cudaFuncGetAttributes(&fa, k));
+  ESC_TRY(allow_max_smem(k, smem_optin));     // the limit is the same for every graph
+  const int bytes = (smem_optin - (int)fa.sharedSizeBytes - 1024) & ~15;
+  const int64_t want = std::max<int64_t>(1, (jbig - n0 + 2) / 2);    // words covering [n0, jbig) in one window
+  plan->windowed = true;
+  plan->threads = 1024;
+  plan->cs = 1;
+  plan->shape = 0;
+  plan->win_words = (int)std::max<int64_t>(1, std::min<int64_t>(bytes / 4, want));
+  // ESC_PAIR_WIN_WORDS: narrower windows, so that small graphs take many (tests)
+  plan->win_words = std::min(plan->win_words, env_int("ESC_PAIR_WIN_WORDS", plan->win_words));
+  plan->wlo = jbig - 2 * (int64_t)plan->win_words;
+  int per_sm = 0;
+  ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan->threads, plan->win_words * 4));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  plan->nclusters = sms * per_sm;
+  return cudaSuccess;
+}
+
 static cudaError_t plan_pair_clusters(bool big, int sms, size_t arr_bytes, int64_t n0, int64_t jbig, int smem_optin,
                                       PairPlan* plan) {
-  // default: the window with one 1024-thread CTA per SM (its window is twice
-  // as wide as two 512-thread CTAs' each); without the window, (512, 2)
-  const bool window = env_int("ESC_PAIR_CLUSTER", 1) == 1 && env_int("ESC_PAIR_WINDOW", 2) != 1;
+  // ESC_PAIR_WINDOW: 3 (default) every rank in successive windows
+  // (k_pairs_win); 2 one window over the top ranks and tagged global counters
+  // below it; 1 no window.  The single window takes one 1024-thread CTA per
+  // SM (its window is twice as wide as two 512-thread CTAs' each); without
+  // the window, (512, 2).
+  const int wmode = env_int("ESC_PAIR_WINDOW", 3);
+  if (wmode >= 3 && env_int("ESC_PAIR_CLUSTER", 1) == 1) return plan_pair_windows(big, sms, n0, jbig, smem_optin, plan);
+  const bool window = env_int("ESC_PAIR_CLUSTER", 1) == 1 && wmode != 1;
   plan->shape = std::min(2, env_int("ESC_PAIR_SHAPE", window ? 3 : 2) - 1);
   plan->threads = plan->shape == 2 ? 1024 : 512;
   const void* k = pairs_grp_fn(big, plan->shape);
@@ -2422,8 +2669,8 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   }
   // the heavy pair items: clusters sharing one counter array each
   PairPlan pplan;
+  int64_t n0 = 0;                               // first rank of degree >= 1 (lower ranks are never counted)
   if (five && pcnt[2] > 0) {
-    int64_t n0 = 0;                             // first rank of degree >= 1 (lower ranks are never counted)
     {
       int64_t lo = 0, hi = n;
       while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (hR[mid + 1] - hR[mid] >= 1) hi = mid; else lo = mid + 1; }
@@ -2447,7 +2694,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   }
   size_t sw32 = sizeof(uint32_t) * (size_t)jbig * grid_sweep + 16;
   size_t sw64 = sizeof(unsigned long long) * (size_t)(n - jbig) * grid_sweep + 16;
-  size_t sw32p = five ? sizeof(uint32_t) * (size_t)jbig * pplan.nclusters + 16 : 16;
+  size_t sw32p = five && !pplan.windowed ? sizeof(uint32_t) * (size_t)jbig * pplan.nclusters + 16 : 16;
   size_t sw64p = five ? sizeof(unsigned long long) * (size_t)(n - jbig) * pplan.nclusters + 16 : 16;
   size_t sw32c = five ? sw32 : 16, sw64c = five ? sw64 : 16;
   DevBuf b_bigA, b_bigB, b_bigC;
@@ -2462,6 +2709,22 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   cudaMemsetAsync(b_bigC.p, 0, sw64c, s);
   TagScratch tsA{b_cntA.as<uint32_t>(), b_bigA.as<unsigned long long>(), jbig, n};
   TagScratch tsB{b_cntB.as<uint32_t>(), b_bigB.as<unsigned long long>(), jbig, n};
+  // the windowed heavy items: per CTA the dense 16-bit counts and the list cursors
+  DevBuf b_g16, b_curs;
+  PairWin pwin{};
+  if (five && pplan.windowed) {
+    pwin.g16_words = (n + 2) / 2;
+    pwin.curs_cap = std::max<int64_t>(maxdeg, 1);
+    ESC_TRY(b_g16.alloc(sizeof(uint32_t) * (size_t)pwin.g16_words * pplan.nclusters));
+    ESC_TRY(b_curs.alloc(sizeof(longlong2) * (size_t)pwin.curs_cap * pplan.nclusters));
+    pwin.g16 = b_g16.as<uint32_t>();
+    pwin.curs = b_curs.as<longlong2>();
+    pwin.side = b_bigB.as<unsigned long long>();      // zeroed above
+    pwin.jbig = jbig;
+    pwin.n = n;
+    pwin.n0 = n0;
+    pwin.win_words = pplan.win_words;
+  }
   TagScratch tsC{b_cntC.as<uint32_t>(), b_bigC.as<unsigned long long>(), jbig, n};
   SweepScratch ssC{nullptr, nullptr, b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(), b_ntC.as<unsigned>(), n};
   const int hcap_l = 8192;
@@ -2562,9 +2825,18 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
       (k_pairs_hash<PH_LARGE_SLOTS><<<grid, PH_LARGE_THREADS, sm1, s>>>(g, pl + n, (int64_t)pcnt[1], pq + 1, tl3, T,
                                                                        accs, d_status), note_launch());
     }
-    if (pcnt[2] > 0)
+    if (pcnt[2] > 0 && pplan.windowed) {
+      const size_t smw = sizeof(uint32_t) * (size_t)pplan.win_words;
+      if (jbig < n)
+        (k_pairs_win<true><<<pplan.nclusters, pplan.threads, smw, s>>>(g, pl + 2 * n, (int64_t)pcnt[2], pq + 2, pwin,
+                                                                      tl3, T, accs, ptasks, d_status), note_launch());
+      else
+        (k_pairs_win<false><<<pplan.nclusters, pplan.threads, smw, s>>>(g, pl + 2 * n, (int64_t)pcnt[2], pq + 2, pwin,
+                                                                       tl3, T, accs, ptasks, d_status), note_launch());
+    } else if (pcnt[2] > 0) {
       ESC_TRY(launch_pairs_grp(jbig < n, pplan, g, pl + 2 * n, (int64_t)pcnt[2], pq + 2, tsB, tl3, T, accs, ptasks,
                                s));
+    }
   }
   mark(5, 1, s);
   // cliques and per-triangle sums (Thms 6, 7, 10, 14)

@@ -32,7 +32,7 @@ def test_apply_sets_and_clears_the_class_knobs(monkeypatch):
 
 def test_every_knob_value_is_in_the_library_range():
     assert set(at.KNOBS["ESC_PAIR_CLUSTER"]) <= {1, 2, 4, 8, 16}
-    assert set(at.KNOBS["ESC_PAIR_WINDOW"]) <= {1, 2}
+    assert set(at.KNOBS["ESC_PAIR_WINDOW"]) <= {1, 2, 3}
     assert set(at.KNOBS["ESC_PAIR_SHAPE"]) <= {1, 2, 3}
     assert max(at.KNOBS["ESC_WHEEL_WARP_MAX"]) <= 1024 and max(at.KNOBS["ESC_CLQ_WARP_DIN"]) <= 512
     assert set(at.KNOBS["ESC_CTA_PER_SM"]) <= set(range(1, 9))

@@ -127,6 +127,41 @@ def test_two_hubs_wide_counts():
     assert_same_census(got, want)
 
 
+@pytest.mark.parametrize("win_words,make", [
+    (1, lambda: gg.petersen()),
+    (1, lambda: gg.complete(30)),
+    (3, lambda: gg.disjoint_union([gg.star(40), gg.complete(12), gg.cycle(7)])),
+    (2, lambda: gg.erdos_renyi(60, 0.3, 5)),
+    (64, lambda: gg.barabasi_albert(2000, 4, 6)),
+    (64, lambda: gg.chung_lu(5000, 2.1, 10, 1000, 3)),
+    (200, lambda: gg.config_rmat(12, 3)),
+    (4096, lambda: gg.chung_lu(20000, 2.1, 10, 2000, 8)),
+], ids=["petersen-w1", "K30-w1", "union-w3", "er60-w2", "ba2000-w64", "cl5000-w64", "rmat12-w200", "cl20000-w4096"])
+def test_pair_sweep_in_many_windows_matches_oracle(win_words, make, monkeypatch):
+    """Every pair-sweep item taken as heavy and counted in windows of
+    2 x win_words ranks (many windows per item: cursors, the dense 16-bit
+    array, the top window on chip); the census equals the oracle's."""
+    monkeypatch.setenv("ESC_PAIR_SMALL_W", "1")
+    monkeypatch.setenv("ESC_PAIR_LARGE_W", "1")
+    monkeypatch.setenv("ESC_PAIR_WIN_WORDS", str(win_words))
+    g = make()
+    assert_same_census(gpu_census(g), oracle.census(g))
+
+
+@pytest.mark.parametrize("mode", ["3", "2", "1"])
+def test_two_hubs_in_every_pair_mode(mode, monkeypatch):
+    """Counts above 2^16 at two hubs (the 64-bit counters of ranks >= jbig)
+    with the windowed heavy items in windows of 8192 ranks, the single window
+    and no window: the stored oracle result."""
+    monkeypatch.setenv("ESC_PAIR_WINDOW", mode)
+    monkeypatch.setenv("ESC_PAIR_WIN_WORDS", "4096")
+    g = gg.two_hubs()
+    gold = _golden("two_hubs")
+    assert gold is not None and gold["sha256"] == graph_hash(g)
+    got = gpu_census(g, device=True)
+    assert_same_census(got, {k: [int(x) for x in gold[k]] for k in ("c3", "c4", "c5", "n3", "n4", "n5")})
+
+
 @pytest.mark.parametrize("make", [lambda: gg.config_er500(1), lambda: gg.complete(40),
                                   lambda: gg.chung_lu(20000, 2.1, 10, 2000, 4), lambda: gg.barabasi_albert(3000, 5, 2),
                                   lambda: gg.disjoint_union([gg.star(3000), gg.complete(70), gg.empty(4)]),

@@ -312,20 +312,26 @@ struct CliqueScratch {
 };
 
 // Bytes of the clique pass's work space for out-degree d (B, K4 accumulators,
-// hash of 2 x pow2(2d) ints, T values).
+// hash of 2 x pow2(2d) ints, T values).  B rows are clique_stride(d) words
+// apart: an odd stride, so the lanes of a warp reading word w of 32 different
+// rows hit different shared-memory banks (an even stride of 2^k words puts them
+// on 32 / 2^k banks).
+static inline __host__ __device__ int clique_stride(int d) { return ((d + 63) >> 6) | 1; }
 static inline size_t clique_space(int d) {
-  int w = (d + 63) >> 6, h = 1;
+  int h = 1;
   while (h < 2 * d) h <<= 1;
-  return sizeof(uint64_t) * ((size_t)d * w + d) + sizeof(int32_t) * (2 * (size_t)h) + sizeof(uint32_t) * d;
+  return sizeof(uint64_t) * ((size_t)d * clique_stride(d) + d) + sizeof(int32_t) * (2 * (size_t)h) +
+         sizeof(uint32_t) * d;
 }
 
-// B rows are symmetric (row a = every neighbour of v_a inside N+(x)).
-__device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int b, const uint64_t* Da,
+// B rows are symmetric (row a = every neighbour of v_a inside N+(x)); W words
+// per row, RS words apart.
+__device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int RS, int a, int b, const uint64_t* Da,
                                             const uint64_t* Db, int DW, bool with_k5, unsigned long long& alpha_out,
                                             unsigned long long& beta_out, unsigned long long& k5_out,
                                             unsigned long long& above_out) {
-  const uint64_t* ra = B + (int64_t)a * W;
-  const uint64_t* rb = B + (int64_t)b * W;
+  const uint64_t* ra = B + (int64_t)a * RS;
+  const uint64_t* rb = B + (int64_t)b * RS;
   unsigned long long alpha = 0, k5 = 0, above = 0;
   for (int w = 0; w < W; ++w) alpha += __popcll(ra[w] & rb[w]);
   // 5-cliques with lowest vertex x and next two v_a < v_b: every c in the
@@ -338,7 +344,7 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int a, int
     while (cm) {
       int c = w * 64 + __ffsll((long long)cm) - 1;
       cm &= cm - 1;
-      const uint64_t* rc = B + (int64_t)c * W;
+      const uint64_t* rc = B + (int64_t)c * RS;
       int u0 = (c + 1) >> 6;
       for (int u = u0; u < W; ++u) {
         uint64_t m = ra[u] & rb[u] & rc[u];
@@ -367,9 +373,9 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
   extern __shared__ uint64_t smem64[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
-  int W_cap = (dmax + 63) >> 6;
-  uint64_t* B = GLOBAL_B ? cs.G + (int64_t)blockIdx.x * cs.g_words : smem64;   // dmax * W_cap
-  unsigned long long* k4x = (unsigned long long*)(B + (int64_t)dmax * W_cap);   // dmax
+  const int RS_cap = clique_stride(dmax);
+  uint64_t* B = GLOBAL_B ? cs.G + (int64_t)blockIdx.x * cs.g_words : smem64;   // dmax * RS_cap
+  unsigned long long* k4x = (unsigned long long*)(B + (int64_t)dmax * RS_cap);  // dmax
   int32_t* hk = (int32_t*)(k4x + dmax);                        // hash_cap
   int32_t* hv = hk + hash_cap;                                 // hash_cap
   uint32_t* Tx = (uint32_t*)(hv + hash_cap);                   // dmax
@@ -387,13 +393,14 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
     int din = (int)(o - ib);
     if (d <= dlo || d > dmax) continue;        // the other launch's item
     int W = (d + 63) >> 6;
+    const int RS = clique_stride(d);
     int DW = (din + 63) >> 6;
     bool use_beta = din > 0 && (int64_t)d * DW <= cs.d_words;
     if (din > 0 && !use_beta && threadIdx.x == 0) set_err(status, DEVERR_SCRATCH);
     int hsz = pow2_at_least(2 * d);
     PosHash H{hk, hv, hsz - 1};
     for (int i = threadIdx.x; i < hsz; i += blockDim.x) hk[i] = -1;
-    for (int64_t i = threadIdx.x; i < (int64_t)d * W; i += blockDim.x) B[i] = 0;
+    for (int64_t i = threadIdx.x; i < (int64_t)d * RS; i += blockDim.x) B[i] = 0;
     for (int i = threadIdx.x; i < d; i += blockDim.x) { k4x[i] = 0; Tx[i] = T[o + i]; }
     if (use_beta)
       for (int64_t i = threadIdx.x; i < (int64_t)d * DW; i += blockDim.x) D[i] = 0;
@@ -406,8 +413,8 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
       for (int64_t q = g.op[v] + lane; q < g.R[v + 1]; q += 32) {
         int b = H.find(g.C[q]);
         if (b >= 0) {
-          atomicOr((unsigned long long*)&B[(int64_t)a * W + (b >> 6)], 1ull << (b & 63));
-          atomicOr((unsigned long long*)&B[(int64_t)b * W + (a >> 6)], 1ull << (a & 63));
+          atomicOr((unsigned long long*)&B[(int64_t)a * RS + (b >> 6)], 1ull << (b & 63));
+          atomicOr((unsigned long long*)&B[(int64_t)b * RS + (a >> 6)], 1ull << (a & 63));
         }
       }
     }
@@ -433,7 +440,7 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
         int b = H.find(w);
         if (b < 0) continue;
         unsigned long long alpha, beta, k5, above;
-        clique_edge(B, W, a, b, use_beta ? D + (int64_t)a * DW : nullptr, use_beta ? D + (int64_t)b * DW : nullptr,
+        clique_edge(B, W, RS, a, b, use_beta ? D + (int64_t)a * DW : nullptr, use_beta ? D + (int64_t)b * DW : nullptr,
                     DW, with_k5, alpha, beta, k5, above);
         la.v[5] += ch2(above);                                    // directed bipyramids on this triangle
         unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
@@ -927,22 +934,40 @@ static constexpr int PAIR_TASK = 32 * 4 * 4;   // lists longer than this are sha
 #endif
 static constexpr int PAIR_SHORT = ESC_PAIR_SHORT;   // lists up to this long are walked by one lane (32: Chung-Lu pairs 40.8 -> 40.2 ms against 64)
 
-// Increments for the entries C[cb .. ce) (one warp, PAIR_ILP loads per lane in flight).
+// A 128-bit sum of 64-bit terms kept as a 64-bit word and a carry count:
+// two 64-bit operations per term in the inner loops instead of a 128-bit add.
+struct Sum128 {
+  unsigned long long lo = 0;
+  unsigned hi = 0;
+  __device__ __forceinline__ void add(unsigned long long x) {
+    lo += x;
+    hi += lo < x ? 1u : 0u;
+  }
+  __device__ __forceinline__ u128 get() const { return ((u128)hi << 64) + lo; }
+};
+
+// C(old, 2) of a counter value below 2^32, exactly in 64 bits (zero for 0 and 1).
+__device__ __forceinline__ unsigned long long pair_c2(uint32_t old) {
+  return ((unsigned long long)old * (old - 1u)) >> 1;           // old = 0: 0 x (2^32 - 1)
+}
+
+// Increments for the entries C[cb .. ce) (one warp, PAIR_ILP loads per lane in
+// flight).  Offsets within the list are 32-bit: a row has fewer than 2^31 entries.
 template <class Inc>
 __device__ __forceinline__ u128 pair_range(const DevGraph& g, int64_t cb, int64_t ce, Inc&& inc) {
   const int lane = threadIdx.x & 31;
-  u128 n13 = 0;
-  for (int64_t q = cb + lane; q < ce; q += 32 * PAIR_ILP) {
+  const int32_t* L = g.C + cb;
+  const int len = (int)(ce - cb);
+  Sum128 n13;
+  for (int q = lane; q < len; q += 32 * PAIR_ILP) {
     int32_t jj[PAIR_ILP];
-    uint32_t oo[PAIR_ILP];
 #pragma unroll
-    for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < ce ? __ldcs(&g.C[q + 32 * u]) : -1;
+    for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < len ? __ldcs(L + q + 32 * u) : -1;
 #pragma unroll
-    for (int u = 0; u < PAIR_ILP; ++u) oo[u] = jj[u] >= 0 ? inc(jj[u]) : 1u;
-#pragma unroll
-    for (int u = 0; u < PAIR_ILP; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;   // zero for old = 0 and 1
+    for (int u = 0; u < PAIR_ILP; ++u)
+      if (jj[u] >= 0) n13.add(pair_c2(inc(jj[u])));
   }
-  return n13;
+  return n13.get();
 }
 
 // defer(cb, ce) may take a long list off the warp (returning true) so that
@@ -962,16 +987,18 @@ __device__ __forceinline__ u128 pair_wedges(const DevGraph& g, int64_t b0, int64
     }
     // short lists: each lane its own; the others one at a time by the warp
     if (ce_l - cb_l <= PAIR_SHORT) {
-      for (int64_t q = cb_l; q < ce_l; q += 4) {
+      const int32_t* L = g.C + cb_l;
+      const int len = (int)(ce_l - cb_l);
+      Sum128 sh13;
+      for (int q = 0; q < len; q += 4) {
         int32_t jj[4];
-        uint32_t oo[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) jj[u] = q + u < ce_l ? __ldcs(&g.C[q + u]) : -1;
+        for (int u = 0; u < 4; ++u) jj[u] = q + u < len ? __ldcs(L + q + u) : -1;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) oo[u] = jj[u] >= 0 ? inc(jj[u]) : 1u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;
+        for (int u = 0; u < 4; ++u)
+          if (jj[u] >= 0) sh13.add(pair_c2(inc(jj[u])));
       }
+      n13 += sh13.get();
     }
     unsigned longm = __ballot_sync(0xffffffffu, ce_l - cb_l > PAIR_SHORT);
     while (longm) {
@@ -1036,7 +1063,8 @@ template <class Get>
 __device__ __forceinline__ u128 pair_diamond_chunk(const DevGraph& g, const TriLists& tl3, const uint32_t* T,
                                                    int64_t i, int64_t xb, int64_t r0, int64_t r1, Get&& get) {
   const int lane = threadIdx.x & 31;
-  u128 n17 = 0;
+  const int32_t i32 = (int32_t)i;
+  Sum128 n17;
   int64_t r = r0 + lane;
   int64_t vb_l = 0;
   uint32_t len_l = 0;
@@ -1047,44 +1075,72 @@ __device__ __forceinline__ u128 pair_diamond_chunk(const DevGraph& g, const TriL
   }
   // short lists: each lane walks its own, a few entries in flight, until it
   // passes i (no entry loaded beyond the next few); long ones: the whole warp
-  // on one list at a time
+  // on one list at a time.  Each term W(i,j) - 2 is below 2^32; a lane adds at
+  // most 2^26 of them per list into 64 bits before the carry-counted sum.
   if (r < r1 && len_l <= PAIR_SHORT) {
-    const int64_t ve = vb_l + len_l;
-    for (int64_t s_ = vb_l; s_ < ve; s_ += 4) {
+    const int32_t* L = tl3.U + vb_l;
+    const int len = (int)len_l;
+    unsigned long long part = 0;
+    for (int q = 0; q < len; q += 4) {
       int32_t jj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) jj[u] = s_ + u < ve ? __ldcs(&tl3.U[s_ + u]) : 0x7fffffff;
+      for (int u = 0; u < 4; ++u) jj[u] = q + u < len ? __ldcs(L + q + u) : 0x7fffffff;
       bool past = false;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (jj[u] < i) n17 += (u128)(get(jj[u]) - 2);
+        if (jj[u] < i32) part += get(jj[u]) - 2u;
         else past = true;
       }
       if (past) break;
     }
+    n17.add(part);
   }
-  unsigned longm = __ballot_sync(0xffffffffu, r < r1 && len_l > PAIR_SHORT);
+  // long lists: each lane first finds how many entries of its list lie below
+  // i (i is in the list: a binary search), then the warp reads exactly those,
+  // one list at a time, in blocks of 32 x PAIR_ILP entries and then 4, 2, 1
+  // and a last partial group of 32, so that no slot past the prefix is issued.
+  const bool lng = r < r1 && len_l > PAIR_SHORT;
+  int pre_l = 0;
+  if (lng) {
+    const int32_t* L = tl3.U + vb_l;
+    int lo = 0, hi = (int)len_l;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(L + mid) < i32) lo = mid + 1;
+      else hi = mid;
+    }
+    pre_l = lo;
+  }
+  unsigned longm = __ballot_sync(0xffffffffu, pre_l > 0);
   while (longm) {
     const int k = __ffs(longm) - 1;
     longm &= longm - 1;
-    int64_t vb = __shfl_sync(0xffffffffu, vb_l, k);
-    int64_t ve = vb + __shfl_sync(0xffffffffu, len_l, k);
-    for (int64_t sb = vb; sb < ve; sb += 32 * PAIR_ILP) {
+    const int32_t* L = tl3.U + __shfl_sync(0xffffffffu, vb_l, k) + lane;
+    const int pre = __shfl_sync(0xffffffffu, pre_l, k);
+    unsigned long long part = 0;             // x, y are common neighbours of i and every j read here
+    int sb = 0;
+    for (; sb + 32 * PAIR_ILP <= pre; sb += 32 * PAIR_ILP) {
       int32_t jj[PAIR_ILP];
-      bool past = false;
 #pragma unroll
-      for (int u = 0; u < PAIR_ILP; ++u) {
-        int64_t s_ = sb + lane + 32 * u;
-        jj[u] = s_ < ve ? __ldcs(&tl3.U[s_]) : 0x7fffffff;
-        if (jj[u] >= i) { jj[u] = -1; past = true; }
-      }
+      for (int u = 0; u < PAIR_ILP; ++u) jj[u] = __ldcs(L + sb + 32 * u);
 #pragma unroll
-      for (int u = 0; u < PAIR_ILP; ++u)
-        if (jj[u] >= 0) n17 += (u128)(get(jj[u]) - 2);   // x, y are common neighbours of i, j
-      if (__any_sync(0xffffffffu, past)) break;
+      for (int u = 0; u < PAIR_ILP; ++u) part += get(jj[u]) - 2u;
     }
+#pragma unroll
+    for (int gsz = PAIR_ILP / 2; gsz >= 1; gsz >>= 1) {
+      if (sb + 32 * gsz <= pre) {
+        int32_t jj[PAIR_ILP / 2];
+#pragma unroll
+        for (int u = 0; u < gsz; ++u) jj[u] = __ldcs(L + sb + 32 * u);
+#pragma unroll
+        for (int u = 0; u < gsz; ++u) part += get(jj[u]) - 2u;
+        sb += 32 * gsz;
+      }
+    }
+    if (sb + lane < pre) part += get(__ldcs(L + sb)) - 2u;
+    n17.add(part);
   }
-  return n17;
+  return n17.get();
 }
 
 // The triangles {i, x, y} with y above x of slot p = (i -> x): positions
@@ -1307,27 +1363,29 @@ __device__ __forceinline__ u128 pair_wedges_win(const DevGraph& g, longlong2* cu
     }
     int64_t cn_l = ce_l;                        // the lane's new cursor
     if (ce_l - cb_l <= PAIR_SHORT) {            // short: each lane walks its own list up to hi
-      int64_t q = cb_l;
-      while (q < ce_l) {
+      const int32_t* L = g.C + cb_l;
+      const int len = (int)(ce_l - cb_l);
+      Sum128 sh13;
+      int q = 0;
+      while (q < len) {
         int32_t jj[4];
-        uint32_t oo[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) jj[u] = q + u < ce_l ? __ldcs(&g.C[q + u]) : 0x7fffffff;
+        for (int u = 0; u < 4; ++u) jj[u] = q + u < len ? __ldcs(L + q + u) : 0x7fffffff;
         int stop = 4;
 #pragma unroll
         for (int u = 3; u >= 0; --u)
           if (jj[u] >= hi) stop = u;            // ascending: the first entry at or above hi
 #pragma unroll
-        for (int u = 0; u < 4; ++u) oo[u] = u < stop ? inc(jj[u]) : 1u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) n13 += (u128)oo[u] * (oo[u] - 1) / 2;
+        for (int u = 0; u < 4; ++u)
+          if (u < stop) sh13.add(pair_c2(inc(jj[u])));
         if (stop < 4) {
           q += stop;
           break;
         }
         q += 4;
       }
-      cn_l = min(q, ce_l);
+      n13 += sh13.get();
+      cn_l = cb_l + min(q, len);
     }
     unsigned longm = __ballot_sync(0xffffffffu, ce_l - cb_l > PAIR_SHORT);
     while (longm) {                             // long: the warp takes them one at a time

@@ -317,6 +317,7 @@ struct CliqueScratch {
 // rows hit different shared-memory banks (an even stride of 2^k words puts them
 // on 32 / 2^k banks).
 static inline __host__ __device__ int clique_stride(int d) { return ((d + 63) >> 6) | 1; }
+static constexpr int CLQ_MAX_WARPS = 16;         // warps of a CTA of the clique pass (512 threads)
 static inline size_t clique_space(int d) {
   int h = 1;
   while (h < 2 * d) h <<= 1;
@@ -326,13 +327,16 @@ static inline size_t clique_space(int d) {
 
 // B rows are symmetric (row a = every neighbour of v_a inside N+(x)); W words
 // per row, RS words apart.
+// with_k5: count the candidates c above b (for DBP); lane_k5: also count the
+// 5-cliques here, one lane per edge (else k5_warp does it for the warp).
 __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int RS, int a, int b, const uint64_t* Da,
-                                            const uint64_t* Db, int DW, bool with_k5, unsigned long long& alpha_out,
-                                            unsigned long long& beta_out, unsigned long long& k5_out,
-                                            unsigned long long& above_out) {
+                                            const uint64_t* Db, int DW, bool with_k5, bool lane_k5,
+                                            unsigned long long& alpha_out, unsigned long long& beta_out,
+                                            unsigned long long& k5_out, unsigned long long& above_out) {
   const uint64_t* ra = B + (int64_t)a * RS;
   const uint64_t* rb = B + (int64_t)b * RS;
   unsigned long long alpha = 0, k5 = 0, above = 0;
+#pragma unroll 4
   for (int w = 0; w < W; ++w) alpha += __popcll(ra[w] & rb[w]);
   // 5-cliques with lowest vertex x and next two v_a < v_b: every c in the
   // common neighbourhood above b, then every l adjacent to a, b, c above c
@@ -341,24 +345,104 @@ __device__ __forceinline__ void clique_edge(const uint64_t* B, int W, int RS, in
     uint64_t cm = ra[w] & rb[w];
     if (w == w0) cm &= ~0ull << ((b + 1) & 63);
     above += __popcll(cm);
-    while (cm) {
+    while (lane_k5 && cm) {
       int c = w * 64 + __ffsll((long long)cm) - 1;
       cm &= cm - 1;
       const uint64_t* rc = B + (int64_t)c * RS;
-      int u0 = (c + 1) >> 6;
-      for (int u = u0; u < W; ++u) {
-        uint64_t m = ra[u] & rb[u] & rc[u];
-        if (u == u0) m &= ~0ull << ((c + 1) & 63);
-        k5 += __popcll(m);
-      }
+      int u = (c + 1) >> 6;
+      if (u < W) k5 += __popcll(ra[u] & rb[u] & rc[u] & (~0ull << ((c + 1) & 63)));
+      // the remaining words four at a time (independent loads in flight)
+      for (++u; u + 4 <= W; u += 4)
+        k5 += __popcll(ra[u] & rb[u] & rc[u]) + __popcll(ra[u + 1] & rb[u + 1] & rc[u + 1]) +
+              __popcll(ra[u + 2] & rb[u + 2] & rc[u + 2]) + __popcll(ra[u + 3] & rb[u + 3] & rc[u + 3]);
+      for (; u < W; ++u) k5 += __popcll(ra[u] & rb[u] & rc[u]);
     }
   }
   unsigned long long beta = 0;
-  if (Da) for (int w = 0; w < DW; ++w) beta += __popcll(Da[w] & Db[w]);
+  if (Da) {
+#pragma unroll 8
+    for (int w = 0; w < DW; ++w) beta += __popcll(Da[w] & Db[w]);
+  }
   alpha_out = alpha;
   beta_out = beta;
   k5_out = k5;
   above_out = above;
+}
+
+// Position of the k-th (0-based) set bit of m (k < popc(m)).
+__device__ __forceinline__ int select32(unsigned m, int k) {
+  int pos = 0, c = __popc(m & 0xffffu);
+  if (k >= c) { k -= c; m >>= 16; pos += 16; }
+  c = __popc(m & 0xffu);
+  if (k >= c) { k -= c; m >>= 8; pos += 8; }
+  c = __popc(m & 0xfu);
+  if (k >= c) { k -= c; m >>= 4; pos += 4; }
+  c = __popc(m & 0x3u);
+  if (k >= c) { k -= c; m >>= 2; pos += 2; }
+  if (k >= (int)(m & 1u)) pos += 1;
+  return pos;
+}
+__device__ __forceinline__ int select64(uint64_t x, int k) {
+  const int c = __popc((unsigned)x);
+  return k < c ? select32((unsigned)x, k) : 32 + select32((unsigned)(x >> 32), k - c);
+}
+
+// 5-cliques (Thm 14) of the edges (a, b) of G[N+(x)] that the lanes hold
+// (want: an edge with at least two candidates), one edge at a time for the
+// whole warp: the candidates c (common neighbours of v_a and v_b above b) are
+// taken 32 at a time, lane k the k-th, and each lane counts the common
+// neighbours of v_a, v_b and v_c above c.  Consecutive candidates lie in the
+// same or neighbouring words, so the lanes' word loops nearly coincide.  The
+// common neighbourhood of a and b goes to the warp's buffer mb (W <= 32 words).
+__device__ __forceinline__ unsigned long long k5_warp(const uint64_t* B, int W, int RS, int a, int b_l, bool want_l,
+                                                      uint64_t* mb) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t* ra = B + (int64_t)a * RS;
+  unsigned long long k5 = 0;
+  unsigned todo = __ballot_sync(0xffffffffu, want_l);
+  while (todo) {
+    const int k = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int b = __shfl_sync(0xffffffffu, b_l, k);
+    const uint64_t* rb = B + (int64_t)b * RS;
+    const int w0 = (b + 1) >> 6;
+    uint64_t m = 0;
+    if (lane >= w0 && lane < W) {
+      m = ra[lane] & rb[lane];
+      if (lane == w0) m &= ~0ull << ((b + 1) & 63);
+    }
+    if (lane < W) mb[lane] = m;
+    __syncwarp();
+    const int cnt = __popcll(m);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int kth = t0 + lane;
+      int wq = w0;                              // the word of candidate kth: words whose candidates all precede it
+      for (int u = w0; u < W; ++u) wq += __shfl_sync(0xffffffffu, incl, u) <= kth ? 1 : 0;
+      wq = min(wq, W - 1);
+      const int before = __shfl_sync(0xffffffffu, incl, wq) - __shfl_sync(0xffffffffu, cnt, wq);
+      if (kth < total) {
+        const int c = wq * 64 + select64(mb[wq], kth - before);
+        const uint64_t* rc = B + (int64_t)c * RS;
+        int u = (c + 1) >> 6;
+        unsigned long long part = 0;
+        if (u < W) part = __popcll(mb[u] & rc[u] & (~0ull << ((c + 1) & 63)));
+        for (++u; u + 4 <= W; u += 4)
+          part += __popcll(mb[u] & rc[u]) + __popcll(mb[u + 1] & rc[u + 1]) + __popcll(mb[u + 2] & rc[u + 2]) +
+                  __popcll(mb[u + 3] & rc[u + 3]);
+        for (; u < W; ++u) part += __popcll(mb[u] & rc[u]);
+        k5 += part;
+      }
+    }
+    __syncwarp();                               // the buffer is read before the next edge writes it
+  }
+  return k5;
 }
 
 // Work-space layout of the CTA path: B (d x W u64), K4 accumulators (d u64),
@@ -373,6 +457,7 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
   extern __shared__ uint64_t smem64[];
   __shared__ u128 sh[32];
   __shared__ int64_t sh_item;
+  __shared__ uint64_t s_mb[CLQ_MAX_WARPS][32];   // k5_warp's buffers
   const int RS_cap = clique_stride(dmax);
   uint64_t* B = GLOBAL_B ? cs.G + (int64_t)blockIdx.x * cs.g_words : smem64;   // dmax * RS_cap
   unsigned long long* k4x = (unsigned long long*)(B + (int64_t)dmax * RS_cap);  // dmax
@@ -430,31 +515,43 @@ __global__ void k_clique_large(DevGraph g, const int32_t* items, int64_t nitems,
     }
     __syncthreads();
     unsigned long long dx = (unsigned long long)(g.R[x + 1] - g.R[x]);
-    // edges (a, b) of G[N+(x)]: scan N+(v_a) again to get the slot of (v_a, v_b)
+    // edges (a, b) of G[N+(x)]: scan N+(v_a) again to get the slot of (v_a, v_b);
+    // the lanes step together so that k5_warp can take the 5-cliques
+    const bool warp_k5 = with_k5 && !GLOBAL_B && W <= 32 && nw <= CLQ_MAX_WARPS;
     for (int a = wid; a < d; a += nw) {
       int32_t v = g.C[o + a];
       unsigned long long dva = (unsigned long long)(g.R[v + 1] - g.R[v]);
       unsigned long long k4a = 0;
-      for (int64_t q = g.op[v] + lane; q < g.R[v + 1]; q += 32) {
-        int32_t w = g.C[q];
-        int b = H.find(w);
-        if (b < 0) continue;
-        unsigned long long alpha, beta, k5, above;
-        clique_edge(B, W, RS, a, b, use_beta ? D + (int64_t)a * DW : nullptr, use_beta ? D + (int64_t)b * DW : nullptr,
-                    DW, with_k5, alpha, beta, k5, above);
-        la.v[5] += ch2(above);                                    // directed bipyramids on this triangle
-        unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
-        unsigned long long tab = T[q], txa = Tx[a], txb = Tx[b];
-        la.v[0] += alpha;                                         // 3 x K4
-        la.v[1] += ch2(alpha + beta);                             // N20
-        la.v[2] += (u128)(tab - 1) * (dx - 2) + (u128)(txb - 1) * (dva - 2) + (u128)(txa - 1) * (dvb - 2);   // N10
-        la.v[3] += (u128)(txa - 1) * (txb - 1) + (u128)(txa - 1) * (tab - 1) + (u128)(txb - 1) * (tab - 1);  // N16
-        la.v[4] += k5;                                            // N21
-        if (alpha) {
-          atomicAdd(&K4e[q], alpha);
-          atomicAdd(&k4x[b], alpha);
-          k4a += alpha;
+      const int64_t qe = g.R[v + 1];
+      for (int64_t qb = g.op[v]; qb < qe; qb += 32) {
+        const int64_t q = qb + lane;
+        int b = -1;
+        int32_t w = 0;
+        if (q < qe) {
+          w = g.C[q];
+          b = H.find(w);
         }
+        unsigned long long above = 0;
+        if (b >= 0) {
+          unsigned long long alpha, beta, k5;
+          clique_edge(B, W, RS, a, b, use_beta ? D + (int64_t)a * DW : nullptr,
+                      use_beta ? D + (int64_t)b * DW : nullptr, DW, with_k5, with_k5 && !warp_k5, alpha, beta, k5,
+                      above);
+          la.v[5] += ch2(above);                                  // directed bipyramids on this triangle
+          unsigned long long dvb = (unsigned long long)(g.R[w + 1] - g.R[w]);
+          unsigned long long tab = T[q], txa = Tx[a], txb = Tx[b];
+          la.v[0] += alpha;                                       // 3 x K4
+          la.v[1] += ch2(alpha + beta);                           // N20
+          la.v[2] += (u128)(tab - 1) * (dx - 2) + (u128)(txb - 1) * (dva - 2) + (u128)(txa - 1) * (dvb - 2);   // N10
+          la.v[3] += (u128)(txa - 1) * (txb - 1) + (u128)(txa - 1) * (tab - 1) + (u128)(txb - 1) * (tab - 1);  // N16
+          la.v[4] += k5;                                          // N21 (zero when k5_warp counts them)
+          if (alpha) {
+            atomicAdd(&K4e[q], alpha);
+            atomicAdd(&k4x[b], alpha);
+            k4a += alpha;
+          }
+        }
+        if (warp_k5) la.v[4] += k5_warp(B, W, RS, a, b, b >= 0 && above >= 2, s_mb[wid]);
       }
       k4a = warp_sum_u64(k4a);
       if (lane == 0 && k4a) atomicAdd(&k4x[a], k4a);
@@ -2641,7 +2738,9 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   // out-degrees up to dsplit keep the bit matrix in shared memory; the few
   // larger ones (dense graphs) use a per-CTA region of global memory
   int dsplit = dmax;
-  while (dsplit > SMALL_DPLUS + 1 && clique_space(dsplit) + 1024 > (size_t)smem_optin) --dsplit;
+  while (dsplit > SMALL_DPLUS + 1 &&
+         clique_space(dsplit) + 1024 + sizeof(uint64_t) * 32 * CLQ_MAX_WARPS > (size_t)smem_optin)
+    --dsplit;
   const int dmax_s = std::min(dmax, dsplit);
   int hcap_b = pow2_at_least(2 * dmax_s);
   size_t smem_b = clique_space(dmax_s);

@@ -824,6 +824,7 @@ static constexpr int SWEEP_ILP = ESC_SWEEP_ILP;   // independent accesses in fli
 #define ESC_PAIR_ILP 8
 #endif
 static constexpr int PAIR_ILP = ESC_PAIR_ILP;
+static_assert(PAIR_ILP >= 1 && PAIR_ILP <= 8, "pair_range sums at most 8 values of C(old, 2) in 64 bits");
 
 struct SweepScratch {
   uint32_t* cnt;       // per CTA: n counters (kept zero between items)
@@ -1060,9 +1061,11 @@ __device__ __forceinline__ u128 pair_range(const DevGraph& g, int64_t cb, int64_
     int32_t jj[PAIR_ILP];
 #pragma unroll
     for (int u = 0; u < PAIR_ILP; ++u) jj[u] = q + 32 * u < len ? __ldcs(L + q + 32 * u) : -1;
+    unsigned long long blk = 0;                 // at most 8 terms below 2^61 (a count is below 2^31)
 #pragma unroll
     for (int u = 0; u < PAIR_ILP; ++u)
-      if (jj[u] >= 0) n13.add(pair_c2(inc(jj[u])));
+      if (jj[u] >= 0) blk += pair_c2(inc(jj[u]));
+    n13.add(blk);
   }
   return n13.get();
 }
@@ -1091,9 +1094,11 @@ __device__ __forceinline__ u128 pair_wedges(const DevGraph& g, int64_t b0, int64
         int32_t jj[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) jj[u] = q + u < len ? __ldcs(L + q + u) : -1;
+        unsigned long long blk = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (jj[u] >= 0) sh13.add(pair_c2(inc(jj[u])));
+          if (jj[u] >= 0) blk += pair_c2(inc(jj[u]));
+        sh13.add(blk);
       }
       n13 += sh13.get();
     }
@@ -1404,13 +1409,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pairs_grp(DevGraph g, const i
 // wrote (a diamond tip j shares two neighbours with i, so W(i,j) >= 2 and its
 // window took increments).
 struct PairWin {
-  uint32_t* g16;              // per CTA: rank j at bits 16 ((j + par) & 1) of word (j + par) >> 1, par = jbig & 1
-  int64_t g16_words;          // (n + 2) / 2
+  uint32_t* g16;              // per CTA: rank j at bits 16 ((j + par) & 1) of word ((j + par) >> 1) + woff
+  int64_t g16_words;          // a multiple of 4, >= (n + 2) / 2 + 4
+  int woff;                   // 0..3: puts the first word of every window on a 16-byte boundary
   longlong2* curs;            // per CTA: (cursor, end) of the list N(c) of every c in N(i)
   int64_t curs_cap;           // >= the largest degree
   unsigned long long* side;   // per CTA: n - jbig counters (tag << 32) | count
   int64_t jbig, n, n0;        // n0: the first rank of degree >= 1
-  int win_words;
+  int win_words;              // a multiple of 4
 };
 
 // First position q in [a, b) with C[q] >= key (C ascending there), or b; one
@@ -1472,9 +1478,11 @@ __device__ __forceinline__ u128 pair_wedges_win(const DevGraph& g, longlong2* cu
 #pragma unroll
         for (int u = 3; u >= 0; --u)
           if (jj[u] >= hi) stop = u;            // ascending: the first entry at or above hi
+        unsigned long long blk = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u < stop) sh13.add(pair_c2(inc(jj[u])));
+          if (u < stop) blk += pair_c2(inc(jj[u]));
+        sh13.add(blk);
         if (stop < 4) {
           q += stop;
           break;
@@ -1512,14 +1520,16 @@ __global__ void __launch_bounds__(1024, 1) k_pairs_win(DevGraph g, const int32_t
   const int64_t grp = blockIdx.x;
   const int64_t S = 2 * (int64_t)pw.win_words;
   const int64_t par = pw.jbig & 1;
-  uint32_t* g16 = pw.g16 + grp * pw.g16_words;
+  uint32_t* g16 = pw.g16 + grp * pw.g16_words + pw.woff;
+  uint4* const win4 = reinterpret_cast<uint4*>(win);
+  const int nv = pw.win_words >> 2;
   longlong2* curs = pw.curs + grp * pw.curs_cap;
   unsigned long long* side = pw.side + grp * (pw.n - pw.jbig);
   uint32_t tag = 0;
   const int ids[2] = {ACC_N13, ACC_N17};
   LocalAcc<2> la;
   la.zero();
-  for (int t = threadIdx.x; t < pw.win_words; t += blockDim.x) win[t] = 0u;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) win4[t] = make_uint4(0u, 0u, 0u, 0u);
   if (threadIdx.x == 0) sh_flag[0] = sh_flag[1] = 0;
   while (true) {
     const int64_t it = next_item(qctr, nitems, &sh_item);   // its barriers publish the cleared window
@@ -1542,6 +1552,7 @@ __global__ void __launch_bounds__(1024, 1) k_pairs_win(DevGraph g, const int32_t
     bool top_touched = false;
     for (int64_t k = kbot; k >= ktop; --k) {
       const int64_t lo = pw.jbig - (k + 1) * S;
+      const uint32_t lo32 = (uint32_t)lo;       // -S <= lo < 2^31: 32-bit differences below
       const bool last = k == ktop;
       const int32_t hi = last ? 0x7fffffff : (int32_t)(pw.jbig - k * S);
       bool tch = false;
@@ -1552,8 +1563,8 @@ __global__ void __launch_bounds__(1024, 1) k_pairs_win(DevGraph g, const int32_t
           atomicMax(q, (unsigned long long)tag << 32);
           return (uint32_t)atomicAdd(q, 1ull);
         }
-        const int64_t q = j - lo;
-        const unsigned s16 = 16u * (unsigned)(q & 1);
+        const uint32_t q = (uint32_t)j - lo32;  // in [0, S)
+        const unsigned s16 = (q & 1u) << 4;
         return (atomicAdd(&win[q >> 1], 1u << s16) >> s16) & 0xffffu;
       };
       n13 += pair_wedges_win(g, curs, b0, e0, wid, nw, k == kbot, last, hi, inc,
@@ -1571,32 +1582,35 @@ __global__ void __launch_bounds__(1024, 1) k_pairs_win(DevGraph g, const int32_t
       if (last) {
         top_touched = touched;
       } else {
-        if (touched) {                          // write the window whole, then clear it
-          const int64_t w0 = (lo + par) >> 1;   // lo + par is even
-          for (int64_t t = threadIdx.x; t < pw.win_words; t += blockDim.x)
-            if (w0 + t >= 0) g16[w0 + t] = win[t];
-          __syncthreads();
-          for (int t = threadIdx.x; t < pw.win_words; t += blockDim.x) win[t] = 0u;
+        if (touched) {                          // write the window whole and clear it, 4 words at a time
+          const int64_t w0 = (lo + par) >> 1;   // lo + par is even; w0 + woff is a multiple of 4
+          uint4* g4 = reinterpret_cast<uint4*>(g16 + w0);
+          for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+            const uint4 v = win4[t];
+            if (pw.woff + w0 + 4 * t >= 0) g4[t] = v;   // the lowest window may start below rank 0
+            win4[t] = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
         __syncthreads();
       }
     }
-    const int64_t lo_top = pw.jbig - (ktop + 1) * S;
+    const uint32_t lo_top32 = (uint32_t)(pw.jbig - (ktop + 1) * S), S32 = (uint32_t)S;
     u128 n17 = pair_diamonds(g, tl3, T, i, b0, e0, wid, nw, [&](int32_t j) -> uint32_t {
+      // j < min(i, jbig) lies in the top window exactly when j - lo_top (mod 2^32) is below S
+      const uint32_t q = (uint32_t)j - lo_top32;
+      if (q < S32) return (win[q >> 1] >> ((q & 1u) << 4)) & 0xffffu;
       if (BIG && j >= pw.jbig) {
         const unsigned long long v = __ldcg(&side[j - pw.jbig]);
         return (uint32_t)(v >> 32) == tag ? (uint32_t)v : 0u;
       }
-      const int64_t q = j - lo_top;
-      if (q >= 0) return (win[q >> 1] >> (16u * (unsigned)(q & 1))) & 0xffffu;
-      const int64_t t = j + par;
-      return (__ldcg(&g16[t >> 1]) >> (16u * (unsigned)(t & 1))) & 0xffffu;
+      const uint32_t t = (uint32_t)j + (uint32_t)par;
+      return (__ldcg(&g16[t >> 1]) >> ((t & 1u) << 4)) & 0xffffu;
     });
     la.v[0] += n13;
     la.v[1] += n17;
     __syncthreads();                            // the diamond reads of the window are done
     if (top_touched)
-      for (int t = threadIdx.x; t < pw.win_words; t += blockDim.x) win[t] = 0u;
+      for (int t = threadIdx.x; t < nv; t += blockDim.x) win4[t] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) sh_flag[0] = sh_flag[1] = 0;
     block_item_flush(la, ids, acc, i, sh);
   }
@@ -2449,14 +2463,15 @@ static cudaError_t plan_pair_windows(bool big, int sms, int64_t n0, int64_t jbig
   ESC_TRY(cudaFuncGetAttributes(&fa, k));
   ESC_TRY(allow_max_smem(k, smem_optin));     // the limit is the same for every graph
   const int bytes = (smem_optin - (int)fa.sharedSizeBytes - 1024) & ~15;
-  const int64_t want = std::max<int64_t>(1, (jbig - n0 + 2) / 2);    // words covering [n0, jbig) in one window
+  const int64_t want = ((jbig - n0 + 2) / 2 + 3) & ~(int64_t)3;     // words covering [n0, jbig) in one window
   plan->windowed = true;
   plan->threads = 1024;
   plan->cs = 1;
   plan->shape = 0;
-  plan->win_words = (int)std::max<int64_t>(1, std::min<int64_t>(bytes / 4, want));
+  plan->win_words = (int)std::min<int64_t>(bytes / 4, want);
   // ESC_PAIR_WIN_WORDS: narrower windows, so that small graphs take many (tests)
   plan->win_words = std::min(plan->win_words, env_int("ESC_PAIR_WIN_WORDS", plan->win_words));
+  plan->win_words = std::max(4, plan->win_words & ~3);          // whole 16-byte vectors
   plan->wlo = jbig - 2 * (int64_t)plan->win_words;
   int per_sm = 0;
   ESC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan->threads, plan->win_words * 4));
@@ -2870,7 +2885,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
   DevBuf b_g16, b_curs;
   PairWin pwin{};
   if (five && pplan.windowed) {
-    pwin.g16_words = (n + 2) / 2;
+    pwin.g16_words = ((n + 2) / 2 + 4 + 3) & ~(int64_t)3;
     pwin.curs_cap = std::max<int64_t>(maxdeg, 1);
     ESC_TRY(b_g16.alloc(sizeof(uint32_t) * (size_t)pwin.g16_words * pplan.nclusters));
     ESC_TRY(b_curs.alloc(sizeof(longlong2) * (size_t)pwin.curs_cap * pplan.nclusters));
@@ -2881,6 +2896,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     pwin.n = n;
     pwin.n0 = n0;
     pwin.win_words = pplan.win_words;
+    pwin.woff = (int)((4 - (((jbig + (jbig & 1)) >> 1) & 3)) & 3);
   }
   TagScratch tsC{b_cntC.as<uint32_t>(), b_bigC.as<unsigned long long>(), jbig, n};
   SweepScratch ssC{nullptr, nullptr, b_cntD.as<uint32_t>(), b_tlD.as<int32_t>(), b_ntC.as<unsigned>(), n};

@@ -1645,14 +1645,14 @@ __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t*
   const int lane = threadIdx.x & 31;
   for (uint32_t ab = a0; ab < lenu; ab += 32 * astep) {
     uint32_t a = ab + lane * astep;
-    int64_t ok_l = 0;
+    const int32_t* Lk_l = tl3.P;
     uint32_t lk_l = 0;
     bool live = a < lenu, in = false;
     if (live) {
       int32_t pk = Lu[a];
       if (pk < pu) {
         in = true;
-        ok_l = tl3.offp[base + pk];
+        Lk_l = tl3.P + tl3.offp[base + pk];
         lk_l = T[base + pk];
       }
     }
@@ -1661,7 +1661,8 @@ __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t*
     while (m) {
       int k = __ffs(m) - 1;
       m &= m - 1;
-      int64_t ok = __shfl_sync(0xffffffffu, ok_l, k);
+      const int32_t* Lk = reinterpret_cast<const int32_t*>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(Lk_l), k));
       uint32_t lk = __shfl_sync(0xffffffffu, lk_l, k);
       for (uint32_t tb = 0; tb < lk; tb += 32 * WHEEL_ILP) {
         int32_t pv[WHEEL_ILP];
@@ -1669,7 +1670,7 @@ __device__ __forceinline__ void wheel_links(const TriLists& tl3, const uint32_t*
 #pragma unroll
         for (int u = 0; u < WHEEL_ILP; ++u) {
           uint32_t t = tb + lane + 32 * u;
-          pv[u] = t < lk ? tl3.P[ok + t] : 0x7fffffff;
+          pv[u] = t < lk ? Lk[t] : 0x7fffffff;
           if (pv[u] >= pu) { pv[u] = -1; past = true; }
         }
 #pragma unroll

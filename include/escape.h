@@ -207,8 +207,9 @@ escape_status escape_last_basis_counts(const escape_graph* g, escape_u128* out);
  * first call on that device -- and keeps it until the process exits; so make
  * the first call on each device before the caller's own pool claims the
  * device's memory.  That first call also looks up the array's device address
- * (one-time set-up per device); make it before any stream capture.  Every
- * call reads a status word back and waits for its stream before returning.
+ * (one-time set-up per device).  Every call reads a status word back and
+ * waits for its stream before returning, so no call may be made while its
+ * stream is being captured into a CUDA graph.
  * No cudaMalloc, cudaFree or allocating library routine is called.
  */
 #define ESCAPE_NOALLOC_MAX_N 32768

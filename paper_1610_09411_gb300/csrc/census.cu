@@ -2482,13 +2482,16 @@ static cudaError_t plan_pair_windows(bool big, int sms, int64_t n0, int64_t jbig
 }
 
 static cudaError_t plan_pair_clusters(bool big, int sms, size_t arr_bytes, int64_t n0, int64_t jbig, int smem_optin,
-                                      PairPlan* plan) {
-  // ESC_PAIR_WINDOW: 3 (default) every rank in successive windows
-  // (k_pairs_win); 2 one window over the top ranks and tagged global counters
-  // below it; 1 no window.  The single window takes one 1024-thread CTA per
-  // SM (its window is twice as wide as two 512-thread CTAs' each); without
-  // the window, (512, 2).
-  const int wmode = env_int("ESC_PAIR_WINDOW", 3);
+                                      bool union_of_graphs, PairPlan* plan) {
+  // ESC_PAIR_WINDOW: 3 every rank in successive windows (k_pairs_win, the
+  // default for one graph); 2 one window over the top ranks and tagged global
+  // counters below it (the default for a batch: in a block-diagonal union the
+  // ranks of one member are spread over the whole rank range, so an item
+  // would walk and write nearly every window for a few hundred wedges); 1 no
+  // window.  The single window takes one 1024-thread CTA per SM (its window
+  // is twice as wide as two 512-thread CTAs' each); without the window,
+  // (512, 2).
+  const int wmode = env_int("ESC_PAIR_WINDOW", union_of_graphs ? 2 : 3);
   if (wmode >= 3 && env_int("ESC_PAIR_CLUSTER", 1) == 1) return plan_pair_windows(big, sms, n0, jbig, smem_optin, plan);
   const bool window = env_int("ESC_PAIR_CLUSTER", 1) == 1 && wmode != 1;
   plan->shape = std::min(2, env_int("ESC_PAIR_SHAPE", window ? 3 : 2) - 1);
@@ -2851,7 +2854,7 @@ cudaError_t run_census(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     }
     size_t arr_bytes = sizeof(uint32_t) * (size_t)std::max<int64_t>(jbig - n0, 0) +
                        sizeof(unsigned long long) * (size_t)(n - jbig);
-    ESC_TRY(plan_pair_clusters(jbig < n, sms, arr_bytes, n0, jbig, smem_optin, &pplan));
+    ESC_TRY(plan_pair_clusters(jbig < n, sms, arr_bytes, n0, jbig, smem_optin, cfg.num_graphs > 1, &pplan));
   }
   // task buffers of the heavy pair items: the largest item has at most
   // w_max / PAIR_TASK + d_max tasks

@@ -45,6 +45,23 @@ def test_batch_mixed_members_match_oracle():
         assert_same_census(r, oracle.census(g))
 
 
+@pytest.mark.parametrize("mode", ["3", "1"])
+def test_batch_in_every_pair_mode_matches_oracle(mode, monkeypatch):
+    """A batch with every pair item taken as heavy, counted in windows of 64
+    ranks (mode 3) or with tagged global counters only (mode 1), instead of
+    the single window batches use by default."""
+    from paper_1610_09411_gb300 import escape as esc
+    monkeypatch.setenv("ESC_PAIR_WINDOW", mode)
+    monkeypatch.setenv("ESC_PAIR_WIN_WORDS", "32")
+    monkeypatch.setenv("ESC_PAIR_SMALL_W", "1")
+    monkeypatch.setenv("ESC_PAIR_LARGE_W", "1")
+    graphs = [gg.complete(9), gg.erdos_renyi(60, 0.3, 4), gg.empty(2), gg.barabasi_albert(120, 4, 2),
+              gg.chung_lu(400, 2.1, 8, 80, 6), gg.petersen()]
+    res = esc.escape_census5_batch(*_pack(graphs))
+    for g, r in zip(graphs, res):
+        assert_same_census(r, oracle.census(g))
+
+
 def test_batch_workload_sample_matches_single_calls():
     from paper_1610_09411_gb300 import escape as esc
     graphs = gg.batch_graphs(24, 17, n_lo=20, n_hi=400)

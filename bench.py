@@ -466,7 +466,8 @@ def run_serve_bench(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 3 for the R-MAT 22 census, about a minute; 5 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
@@ -475,6 +476,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-rates", default="100,1000,10000")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 3 if args.workload == "rmat22" else 5
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

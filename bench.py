@@ -50,7 +50,7 @@ ALG_BYTES = {
     "wheels": ("k_wheels_cta / k_wheels_warp", "4 B x D (one id read per diamond, Thm 11 wheel sweep)",
                lambda s: 4 * s["D"]),
     "pairs": ("k_pairs", "4 B x (W + D) (one id read per wedge and per diamond, Thms 11-12; kernels "
-              "k_pair_classify, k_pairs_hash<4096>, k_pairs_hash<16384>, k_pairs_grp)",
+              "k_pair_classify, k_pairs_hash<4096>, k_pairs_hash<16384>, k_pairs_win)",
               lambda s: 4 * (s["W"] + s["D"])),
     "cliques": ("k_clique_large / k_clique_warp", "4 B x (2 W++ + W+-) adjacency reads of the bit-matrix builds",
                 lambda s: None),

@@ -1881,10 +1881,12 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
       int kmax = (int)min((int64_t)32, (e0 - pbase + nw - 1) / nw);
       for (int k = 0; k < kmax; ++k) {
         int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
-        for (int64_t q = cb + lane; q < ce; q += 32 * SWEEP_ILP) {
+        const int32_t* L = g.C + cb;            // 32-bit offsets: a row has fewer than 2^31 entries
+        const int len = (int)(ce - cb);
+        for (int q = lane; q < len; q += 32 * SWEEP_ILP) {
           int32_t jj[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < len ? L[q + 32 * u] : (int32_t)i;
 #pragma unroll
           for (int u = 0; u < SWEEP_ILP; ++u)
             if (jj[u] != i) wp.add(jj[u]);
@@ -1903,11 +1905,13 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
       int kmax = (int)min((int64_t)32, (o - pbase + nw - 1) / nw);
       for (int k = 0; k < kmax; ++k) {
         int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
-        for (int64_t q = cb + lane; q < ce; q += 32 * SWEEP_ILP) {
+        const int32_t* L = g.C + cb;
+        const int len = (int)(ce - cb);
+        for (int q = lane; q < len; q += 32 * SWEEP_ILP) {
           int32_t bb[SWEEP_ILP];
           uint32_t oo[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) bb[u] = q + 32 * u < ce ? g.C[q + 32 * u] : (int32_t)i;
+          for (int u = 0; u < SWEEP_ILP; ++u) bb[u] = q + 32 * u < len ? L[q + 32 * u] : (int32_t)i;
 #pragma unroll
           for (int u = 0; u < SWEEP_ILP; ++u) oo[u] = bb[u] != i ? atomicAdd(&p2[bb[u]], 1u) : 1u;
 #pragma unroll
@@ -1934,10 +1938,12 @@ __global__ void __launch_bounds__(512, 2) k_cycles5(DevGraph g, unsigned long lo
         int64_t cb = __shfl_sync(0xffffffffu, cb_l, k), ce = __shfl_sync(0xffffffffu, ce_l, k);
         uint32_t pk = __shfl_sync(0xffffffffu, pk_l, k);
         unsigned long long s_ = 0;
-        for (int64_t q = cb + lane; q < ce; q += 32 * SWEEP_ILP) {
+        const int32_t* L = g.C + cb;
+        const int len = (int)(ce - cb);
+        for (int q = lane; q < len; q += 32 * SWEEP_ILP) {
           int32_t jj[SWEEP_ILP];
 #pragma unroll
-          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < ce ? g.C[q + 32 * u] : -1;
+          for (int u = 0; u < SWEEP_ILP; ++u) jj[u] = q + 32 * u < len ? L[q + 32 * u] : -1;
 #pragma unroll
           for (int u = 0; u < SWEEP_ILP; ++u)
             if (jj[u] >= 0) s_ += wp.get(jj[u]);

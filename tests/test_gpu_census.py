@@ -308,6 +308,16 @@ def test_rmat_scale22_full_size():
             assert got[key] == [int(x) for x in gold[key]], key
     assert sum(got["c5"]) == comb(n, 5) and sum(got["c4"]) == comb(n, 4) and sum(got["c3"]) == comb(n, 3)
     assert min(got["c5"] + got["c4"]) >= 0
+    # the oracle's wedges, triangles and diamonds of this graph (stored): the
+    # non-induced wedge, triangle and diamond counts
+    sums_path = os.path.join(GOLDEN, "sums_rmat22.json")
+    if os.path.exists(sums_path):
+        with open(sums_path) as f:
+            sums = json.load(f)
+        assert sums["sha256"] == graph_hash(g)
+        assert got["n3"][2] == int(sums["sums"]["W"])
+        assert got["n3"][3] == int(sums["sums"]["T"])
+        assert got["n4"][4] == int(sums["sums"]["D"])
     pe = got["per_element"]
     T = got["n3"][3]
     assert int(pe["T_e"].sum()) == 6 * T and int(pe["t_i"].sum()) == 3 * T

@@ -299,3 +299,6 @@ def test_wedge_diamond_sums_equal_the_census_sums():
             assert w["W"] == b["c3"][2] + 3 * b["c3"][3]
             assert w["T"] == b["c3"][3]
             assert w["D"] == b["c4"][4] + 6 * b["c4"][5]
+        # the same sums are the census's non-induced wedges, triangles and diamonds
+        c = oracle.census(g)
+        assert (c["n3"][2], c["n3"][3], c["n4"][4]) == (w["W"], w["T"], w["D"]), g.name

@@ -93,6 +93,8 @@ def _load(parallel: bool = False):
         lib.oracle_vertex_elements.argtypes = [i64, P, P, i64, P, P, P]
         lib.oracle_wedge_diamond_sums.restype = c_int
         lib.oracle_wedge_diamond_sums.argtypes = [i64, P, P, P]
+        lib.oracle_pair_sums.restype = c_int
+        lib.oracle_pair_sums.argtypes = [i64, P, P, P]
         lib.oracle_num_sums.restype = c_int
         lib.oracle_num_threads.restype = c_int
         assert lib.oracle_num_sums() == len(SUM_NAMES)
@@ -283,6 +285,18 @@ def wedge_diamond_sums(g, parallel: bool = False) -> dict:
         raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
     vals = [int(out[2 * k]) | (int(out[2 * k + 1]) << 64) for k in range(3)]
     return dict(zip(("W", "T", "D"), vals))
+
+
+def pair_sums(g, parallel: bool = False) -> dict:
+    """C4 (4-cycles) and N13 (non-induced K2,3) from the two-hop pair counts
+    W(i,j) = |N(i) cap N(j)|, without the rest of the census."""
+    rp, col = _csr(g)
+    out = np.zeros(4, dtype=np.uint64)
+    rc = _load(parallel).oracle_pair_sums(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data)
+    if rc:
+        raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
+    vals = [int(out[2 * k]) | (int(out[2 * k + 1]) << 64) for k in range(2)]
+    return dict(zip(("C4", "N13"), vals))
 
 
 def edge_elements(g, us, vs) -> dict:

@@ -891,6 +891,59 @@ int oracle_wedge_diamond_sums(int64_t n, const int64_t* rp, const int32_t* col, 
   return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Pair sums alone (Thm 5 and the K2,3 term of Thm 11; for graphs whose */
+/* full census is out of reach).  W(i,j) = |N(i) cap N(j)| is counted  */
+/* by two-hop walks i - c - j from every i:                             */
+/*   C4  = (1/4) sum_i sum_{j != i} C(W(i,j), 2)  (each 4-cycle has two  */
+/*         opposite pairs, each seen from both ends),                    */
+/*   N13 = sum_{i<j} C(W(i,j), 3)  (non-induced K2,3).                   */
+/* out: 2 entries of two u64 words (lo, hi): C4, N13.                   */
+/* ------------------------------------------------------------------ */
+int oracle_pair_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_t* out) {
+  int rc = validate(n, rp, col);
+  if (rc) return rc;
+  g_ovf = 0;
+  const int nw = oracle_num_threads();
+  u128* part = (u128*)calloc((size_t)nw * 2, sizeof(u128));
+  int64_t* scratch = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)(n + 1) * (size_t)nw);
+  if (!part || !scratch) { free(part); free(scratch); return ORACLE_ENOMEM; }
+#pragma omp parallel
+  {
+    const int t = thread_id();
+    int64_t* stamp = scratch + (size_t)t * 3 * (size_t)(n + 1);
+    int64_t* cnt = stamp + (n + 1);
+    int64_t* touched = cnt + (n + 1);
+    for (int64_t v = 0; v <= n; ++v) stamp[v] = -1;
+    u128* mine = part + 2 * t;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t nt = 0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int64_t c = col[p];
+        for (int64_t q = rp[c]; q < rp[c + 1]; ++q) {
+          int64_t j = col[q];
+          if (j == i) continue;
+          if (stamp[j] != i) { stamp[j] = i; cnt[j] = 0; touched[nt++] = j; }
+          cnt[j]++;
+        }
+      }
+      for (int64_t a = 0; a < nt; ++a) {
+        int64_t j = touched[a];
+        mine[0] = add(mine[0], ch2((uint64_t)cnt[j]));
+        if (j > i) mine[1] = add(mine[1], ch3((uint64_t)cnt[j]));
+      }
+    }
+  }
+  u128 S4 = 0, N13 = 0;
+  for (int t = 0; t < nw; ++t) { S4 = add(S4, part[2 * t]); N13 = add(N13, part[2 * t + 1]); }
+  free(part);
+  free(scratch);
+  u128 vals[2] = {S4 / 4, N13};
+  for (int k = 0; k < 2; ++k) { out[2 * k] = (uint64_t)vals[k]; out[2 * k + 1] = (uint64_t)(vals[k] >> 64); }
+  return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
+}
+
 int oracle_edge_elements(int64_t n, const int64_t* rp, const int32_t* col, int64_t count,
                          const int64_t* us, const int64_t* vs, uint64_t* T, uint64_t* K4, uint64_t* C4) {
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));

@@ -9,6 +9,7 @@ computed for (and recompute them live if not).
     python tests/golden/make_golden.py --parallel rmat20 batch24
     python tests/golden/make_golden.py --elements rmat22
     python tests/golden/make_golden.py --parallel --sums rmat22
+    python tests/golden/make_golden.py --parallel --pairs rmat22
 
 --parallel runs the OpenMP build of the same oracle source on OMP_NUM_THREADS
 threads (its equality with the serial build is pinned in test_oracle_pins).
@@ -128,6 +129,21 @@ def write_sums(name, parallel=False):
     print(name, "sums", out["oracle_seconds"], "s")
 
 
+def write_pairs(name, parallel=False):
+    """C4 and N13 (non-induced K2,3) of a workload from the two-hop pair counts
+    alone (oracle.pair_sums), where the full census is out of reach."""
+    g = WORKLOADS[name]()
+    t0 = time.time()
+    w = oracle.pair_sums(g, parallel=parallel)
+    out = {"workload": name, "graph": g.name, "n": g.n, "m": g.m, "sha256": graph_hash(g),
+           "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": oracle.num_threads(parallel),
+           "oracle_host": f"{platform.machine()}, {os.cpu_count()} cores",
+           "sums": {k: str(v) for k, v in w.items()}}
+    with open(os.path.join(HERE, f"pairs_{name}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, "pairs", out["oracle_seconds"], "s")
+
+
 if __name__ == "__main__":
     par = "--parallel" in sys.argv
     names = [a for a in sys.argv[1:] if not a.startswith("--")]
@@ -136,5 +152,7 @@ if __name__ == "__main__":
             write_elements(name)
         elif "--sums" in sys.argv:
             write_sums(name, par)
+        elif "--pairs" in sys.argv:
+            write_pairs(name, par)
         else:
             write(name, par)

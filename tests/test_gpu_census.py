@@ -318,6 +318,15 @@ def test_rmat_scale22_full_size():
         assert got["n3"][2] == int(sums["sums"]["W"])
         assert got["n3"][3] == int(sums["sums"]["T"])
         assert got["n4"][4] == int(sums["sums"]["D"])
+    # the oracle's pair sums (two-hop counts W(i,j) from every vertex): the
+    # 4-cycles and the non-induced K2,3 (class 13 of the connected patterns)
+    pairs_path = os.path.join(GOLDEN, "pairs_rmat22.json")
+    if os.path.exists(pairs_path):
+        with open(pairs_path) as f:
+            pairs = json.load(f)
+        assert pairs["sha256"] == graph_hash(g)
+        assert got["n4"][3] == int(pairs["sums"]["C4"])
+        assert got["n5"][12] == int(pairs["sums"]["N13"])
     pe = got["per_element"]
     T = got["n3"][3]
     assert int(pe["T_e"].sum()) == 6 * T and int(pe["t_i"].sum()) == 3 * T

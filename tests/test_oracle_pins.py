@@ -302,3 +302,17 @@ def test_wedge_diamond_sums_equal_the_census_sums():
         # the same sums are the census's non-induced wedges, triangles and diamonds
         c = oracle.census(g)
         assert (c["n3"][2], c["n3"][3], c["n4"][4]) == (w["W"], w["T"], w["D"]), g.name
+
+
+def test_pair_sums_equal_the_census_and_closed_forms():
+    """C4 and N13 (non-induced K2,3, class 13 of the connected patterns) from
+    the two-hop pair counts alone agree with the census (serial and OpenMP
+    builds) and with the closed forms of K_n and K_{2,b}."""
+    for g in _graphs_small() + [gg.chung_lu(3000, 2.1, 8, 300, 5), gg.config_rmat(11, 2)]:
+        c = oracle.census(g)
+        for par in (False, True):
+            assert oracle.pair_sums(g, parallel=par) == {"C4": c["n4"][3], "N13": c["n5"][12]}, g.name
+    for n in (4, 5, 9, 17):
+        assert oracle.pair_sums(gg.complete(n)) == {"C4": 3 * comb(n, 4), "N13": comb(n, 2) * comb(n - 2, 3)}
+    for b in (1, 2, 3, 7, 30):
+        assert oracle.pair_sums(gg.complete_bipartite(2, b)) == {"C4": comb(b, 2), "N13": comb(b, 3)}

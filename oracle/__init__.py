@@ -95,6 +95,8 @@ def _load(parallel: bool = False):
         lib.oracle_wedge_diamond_sums.argtypes = [i64, P, P, P]
         lib.oracle_pair_sums.restype = c_int
         lib.oracle_pair_sums.argtypes = [i64, P, P, P]
+        lib.oracle_clique4_count.restype = c_int
+        lib.oracle_clique4_count.argtypes = [i64, P, P, P]
         lib.oracle_num_sums.restype = c_int
         lib.oracle_num_threads.restype = c_int
         assert lib.oracle_num_sums() == len(SUM_NAMES)
@@ -297,6 +299,17 @@ def pair_sums(g, parallel: bool = False) -> dict:
         raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
     vals = [int(out[2 * k]) | (int(out[2 * k + 1]) << 64) for k in range(2)]
     return dict(zip(("C4", "N13"), vals))
+
+
+def clique4_count(g, parallel: bool = False) -> int:
+    """The number of 4-cliques, each counted once at its lowest vertex in the
+    degree order as a triangle of G[N+(x)], without the rest of the census."""
+    rp, col = _csr(g)
+    out = np.zeros(2, dtype=np.uint64)
+    rc = _load(parallel).oracle_clique4_count(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data)
+    if rc:
+        raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
+    return int(out[0]) | (int(out[1]) << 64)
 
 
 def edge_elements(g, us, vs) -> dict:

@@ -944,6 +944,78 @@ int oracle_pair_sums(int64_t n, const int64_t* rp, const int32_t* col, uint64_t*
   return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* 4-cliques alone (Thm 6; for graphs whose full census is out of      */
+/* reach): every K4 once, at its lowest vertex x in the degree order    */
+/* (Sec. 3.2, ties by id), as a triangle a < b < c of G[N+(x)]:         */
+/*   K4 = sum_x #{(a, b, c) : a in N+(x), b in N+(a) cap N+(x),         */
+/*                            c in N+(b) cap N+(a) cap N+(x)}.          */
+/* out: two u64 words (lo, hi).                                         */
+/* ------------------------------------------------------------------ */
+int oracle_clique4_count(int64_t n, const int64_t* rp, const int32_t* col, uint64_t* out) {
+  int rc = validate(n, rp, col);
+  if (rc) return rc;
+  g_ovf = 0;
+  G g = {0};
+  g.n = n;
+  g.rp = rp;
+  g.col = col;
+  g.deg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* orp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!g.deg || !orp) { free(g.deg); free(orp); return ORACLE_ENOMEM; }
+  for (int64_t v = 0; v < n; ++v) g.deg[v] = rp[v + 1] - rp[v];
+  /* out-neighbour lists N+(v) = {w in N(v) : v precedes w}, ascending ids */
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t k = 0;
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) k += prec(&g, v, col[p]);
+    orp[v + 1] = orp[v] + k;
+  }
+  int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(orp[n] + 1));
+  const int nw = oracle_num_threads();
+  u128* part = (u128*)calloc((size_t)nw, sizeof(u128));
+  int64_t* marks = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)(n + 1) * (size_t)nw);
+  if (!ocol || !part || !marks) { free(g.deg); free(orp); free(ocol); free(part); free(marks); return ORACLE_ENOMEM; }
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t k = orp[v];
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p)
+      if (prec(&g, v, col[p])) ocol[k++] = col[p];
+  }
+#pragma omp parallel
+  {
+    const int t = thread_id();
+    int64_t* in_x = marks + (size_t)t * 2 * (size_t)(n + 1);   /* in_x[v] == x: v in N+(x) */
+    int64_t* in_a = in_x + (n + 1);                              /* in_a[v] == a: v in N+(a) cap N+(x) */
+    for (int64_t v = 0; v <= n; ++v) { in_x[v] = -1; in_a[v] = -1; }
+    u128 mine = 0;
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t x = 0; x < n; ++x) {
+      for (int64_t p = orp[x]; p < orp[x + 1]; ++p) in_x[ocol[p]] = x;
+      for (int64_t p = orp[x]; p < orp[x + 1]; ++p) {
+        int64_t a = ocol[p];
+        for (int64_t q = orp[a]; q < orp[a + 1]; ++q)
+          if (in_x[ocol[q]] == x) in_a[ocol[q]] = a;
+        for (int64_t q = orp[a]; q < orp[a + 1]; ++q) {
+          int64_t b = ocol[q];
+          if (in_x[b] != x) continue;
+          uint64_t k = 0;
+          for (int64_t r = orp[b]; r < orp[b + 1]; ++r) {
+            int64_t c = ocol[r];
+            if (in_x[c] == x && in_a[c] == a) ++k;
+          }
+          mine = add(mine, k);
+        }
+      }
+    }
+    part[t] = mine;
+  }
+  u128 K4 = 0;
+  for (int t = 0; t < nw; ++t) K4 = add(K4, part[t]);
+  free(g.deg); free(orp); free(ocol); free(part); free(marks);
+  out[0] = (uint64_t)K4;
+  out[1] = (uint64_t)(K4 >> 64);
+  return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
+}
+
 int oracle_edge_elements(int64_t n, const int64_t* rp, const int32_t* col, int64_t count,
                          const int64_t* us, const int64_t* vs, uint64_t* T, uint64_t* K4, uint64_t* C4) {
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));

@@ -10,6 +10,7 @@ computed for (and recompute them live if not).
     python tests/golden/make_golden.py --elements rmat22
     python tests/golden/make_golden.py --parallel --sums rmat22
     python tests/golden/make_golden.py --parallel --pairs rmat22
+    python tests/golden/make_golden.py --parallel --cliques rmat22
 
 --parallel runs the OpenMP build of the same oracle source on OMP_NUM_THREADS
 threads (its equality with the serial build is pinned in test_oracle_pins).
@@ -144,6 +145,21 @@ def write_pairs(name, parallel=False):
     print(name, "pairs", out["oracle_seconds"], "s")
 
 
+def write_cliques(name, parallel=False):
+    """The 4-clique count of a workload alone (oracle.clique4_count), where the
+    full census is out of reach."""
+    g = WORKLOADS[name]()
+    t0 = time.time()
+    k4 = oracle.clique4_count(g, parallel=parallel)
+    out = {"workload": name, "graph": g.name, "n": g.n, "m": g.m, "sha256": graph_hash(g),
+           "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": oracle.num_threads(parallel),
+           "oracle_host": f"{platform.machine()}, {os.cpu_count()} cores",
+           "sums": {"K4": str(k4)}}
+    with open(os.path.join(HERE, f"cliques_{name}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, "cliques", out["oracle_seconds"], "s")
+
+
 if __name__ == "__main__":
     par = "--parallel" in sys.argv
     names = [a for a in sys.argv[1:] if not a.startswith("--")]
@@ -154,5 +170,7 @@ if __name__ == "__main__":
             write_sums(name, par)
         elif "--pairs" in sys.argv:
             write_pairs(name, par)
+        elif "--cliques" in sys.argv:
+            write_cliques(name, par)
         else:
             write(name, par)

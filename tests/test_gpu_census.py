@@ -327,6 +327,13 @@ def test_rmat_scale22_full_size():
         assert pairs["sha256"] == graph_hash(g)
         assert got["n4"][3] == int(pairs["sums"]["C4"])
         assert got["n5"][12] == int(pairs["sums"]["N13"])
+    # the oracle's 4-clique count
+    cliques_path = os.path.join(GOLDEN, "cliques_rmat22.json")
+    if os.path.exists(cliques_path):
+        with open(cliques_path) as f:
+            cliques = json.load(f)
+        assert cliques["sha256"] == graph_hash(g)
+        assert got["n4"][5] == int(cliques["sums"]["K4"])
     pe = got["per_element"]
     T = got["n3"][3]
     assert int(pe["T_e"].sum()) == 6 * T and int(pe["t_i"].sum()) == 3 * T

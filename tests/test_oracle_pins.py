@@ -316,3 +316,17 @@ def test_pair_sums_equal_the_census_and_closed_forms():
         assert oracle.pair_sums(gg.complete(n)) == {"C4": 3 * comb(n, 4), "N13": comb(n, 2) * comb(n - 2, 3)}
     for b in (1, 2, 3, 7, 30):
         assert oracle.pair_sums(gg.complete_bipartite(2, b)) == {"C4": comb(b, 2), "N13": comb(b, 3)}
+
+
+def test_clique4_count_equals_the_census_and_closed_forms():
+    """The 4-cliques counted alone (each at its lowest vertex, as a triangle
+    of G[N+(x)]) agree with the census (serial and OpenMP builds), with
+    C(n,4) on K_n and with zero on triangle-free graphs."""
+    for g in _graphs_small() + [gg.chung_lu(3000, 2.1, 8, 300, 5), gg.config_rmat(11, 2)]:
+        k4 = oracle.census(g)["n4"][5]
+        for par in (False, True):
+            assert oracle.clique4_count(g, parallel=par) == k4, g.name
+    for n in (3, 4, 5, 12, 30):
+        assert oracle.clique4_count(gg.complete(n)) == comb(n, 4)
+    for g in (gg.complete_bipartite(7, 9), gg.petersen(), gg.cycle(12)):
+        assert oracle.clique4_count(g) == 0

@@ -97,6 +97,8 @@ def _load(parallel: bool = False):
         lib.oracle_pair_sums.argtypes = [i64, P, P, P]
         lib.oracle_clique4_count.restype = c_int
         lib.oracle_clique4_count.argtypes = [i64, P, P, P]
+        lib.oracle_clique5_count.restype = c_int
+        lib.oracle_clique5_count.argtypes = [i64, P, P, P]
         lib.oracle_num_sums.restype = c_int
         lib.oracle_num_threads.restype = c_int
         assert lib.oracle_num_sums() == len(SUM_NAMES)
@@ -307,6 +309,18 @@ def clique4_count(g, parallel: bool = False) -> int:
     rp, col = _csr(g)
     out = np.zeros(2, dtype=np.uint64)
     rc = _load(parallel).oracle_clique4_count(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data)
+    if rc:
+        raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
+    return int(out[0]) | (int(out[1]) << 64)
+
+
+def clique5_count(g, parallel: bool = False) -> int:
+    """The number of 5-cliques, each counted once at its lowest vertex in the
+    degree order as a 4-clique of G[N+(x)] (bit sets and popcounts), without
+    the rest of the census."""
+    rp, col = _csr(g)
+    out = np.zeros(2, dtype=np.uint64)
+    rc = _load(parallel).oracle_clique5_count(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data)
     if rc:
         raise ValueError(ORACLE_ERRORS.get(rc, f"oracle error {rc}"))
     return int(out[0]) | (int(out[1]) << 64)

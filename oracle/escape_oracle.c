@@ -1016,6 +1016,104 @@ int oracle_clique4_count(int64_t n, const int64_t* rp, const int32_t* col, uint6
   return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* 5-cliques alone (Thm 14; for graphs whose full census is out of      */
+/* reach): every K5 once, at its lowest vertex x in the degree order, as */
+/* a 4-clique a < b < c < e of H = G[N+(x)] (indices in N+(x)):          */
+/*   K5 = sum_x sum over edges (a, b), a < b, of H and c in             */
+/*        NH(a) cap NH(b) above b of |NH(a) cap NH(b) cap NH(c) above c|, */
+/* with the neighbourhoods NH as bit sets over N+(x) and the sizes by   */
+/* popcount.  out: two u64 words (lo, hi).                              */
+/* ------------------------------------------------------------------ */
+int oracle_clique5_count(int64_t n, const int64_t* rp, const int32_t* col, uint64_t* out) {
+  int rc = validate(n, rp, col);
+  if (rc) return rc;
+  g_ovf = 0;
+  G g = {0};
+  g.n = n;
+  g.rp = rp;
+  g.col = col;
+  g.deg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* orp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!g.deg || !orp) { free(g.deg); free(orp); return ORACLE_ENOMEM; }
+  for (int64_t v = 0; v < n; ++v) g.deg[v] = rp[v + 1] - rp[v];
+  int64_t dmax = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t k = 0;
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) k += prec(&g, v, col[p]);
+    orp[v + 1] = orp[v] + k;
+    if (k > dmax) dmax = k;
+  }
+  const int64_t wmax = (dmax + 63) / 64;
+  int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(orp[n] + 1));
+  const int nw = oracle_num_threads();
+  u128* part = (u128*)calloc((size_t)nw, sizeof(u128));
+  int32_t* posa = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1) * (size_t)nw);
+  uint64_t* bits = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(dmax * wmax + 1) * (size_t)nw);
+  if (!ocol || !part || !posa || !bits) {
+    free(g.deg); free(orp); free(ocol); free(part); free(posa); free(bits);
+    return ORACLE_ENOMEM;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t k = orp[v];
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p)
+      if (prec(&g, v, col[p])) ocol[k++] = col[p];
+  }
+#pragma omp parallel
+  {
+    const int t = thread_id();
+    int32_t* pos = posa + (size_t)t * (size_t)(n + 1);          /* pos[v] = index of v in N+(x), or -1 */
+    uint64_t* B = bits + (size_t)t * (size_t)(dmax * wmax + 1);  /* row a of H: NH(a) as a bit set */
+    for (int64_t v = 0; v <= n; ++v) pos[v] = -1;
+    u128 mine = 0;
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t x = 0; x < n; ++x) {
+      const int64_t d = orp[x + 1] - orp[x];
+      if (d < 4) continue;
+      const int64_t W = (d + 63) / 64;
+      for (int64_t a = 0; a < d; ++a) pos[ocol[orp[x] + a]] = (int32_t)a;
+      memset(B, 0, sizeof(uint64_t) * (size_t)(d * W));
+      for (int64_t a = 0; a < d; ++a) {
+        int64_t va = ocol[orp[x] + a];
+        for (int64_t q = orp[va]; q < orp[va + 1]; ++q) {
+          int64_t b = pos[ocol[q]];
+          if (b < 0) continue;
+          B[a * W + b / 64] |= 1ull << (b % 64);
+          B[b * W + a / 64] |= 1ull << (a % 64);
+        }
+      }
+      for (int64_t a = 0; a < d; ++a)
+        for (int64_t b = a + 1; b < d; ++b) {
+          if (!((B[a * W + b / 64] >> (b % 64)) & 1)) continue;
+          /* c: the common neighbours of a and b above b, word by word */
+          for (int64_t wc = (b + 1) / 64; wc < W; ++wc) {
+            uint64_t cm = B[a * W + wc] & B[b * W + wc];
+            if (wc == (b + 1) / 64) cm &= ~0ull << ((b + 1) % 64);
+            while (cm) {
+              const int64_t c = wc * 64 + __builtin_ctzll(cm);
+              cm &= cm - 1;
+              uint64_t k = 0;   /* e above c adjacent to a, b and c */
+              for (int64_t w = (c + 1) / 64; w < W; ++w) {
+                uint64_t m = B[a * W + w] & B[b * W + w] & B[c * W + w];
+                if (w == (c + 1) / 64) m &= ~0ull << ((c + 1) % 64);
+                k += (uint64_t)__builtin_popcountll(m);
+              }
+              mine = add(mine, k);
+            }
+          }
+        }
+      for (int64_t a = 0; a < d; ++a) pos[ocol[orp[x] + a]] = -1;
+    }
+    part[t] = mine;
+  }
+  u128 K5 = 0;
+  for (int t = 0; t < nw; ++t) K5 = add(K5, part[t]);
+  free(g.deg); free(orp); free(ocol); free(part); free(posa); free(bits);
+  out[0] = (uint64_t)K5;
+  out[1] = (uint64_t)(K5 >> 64);
+  return g_ovf ? ORACLE_EOVERFLOW : ORACLE_OK;
+}
+
 int oracle_edge_elements(int64_t n, const int64_t* rp, const int32_t* col, int64_t count,
                          const int64_t* us, const int64_t* vs, uint64_t* T, uint64_t* K4, uint64_t* C4) {
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));

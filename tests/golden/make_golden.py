@@ -11,6 +11,7 @@ computed for (and recompute them live if not).
     python tests/golden/make_golden.py --parallel --sums rmat22
     python tests/golden/make_golden.py --parallel --pairs rmat22
     python tests/golden/make_golden.py --parallel --cliques rmat22
+    python tests/golden/make_golden.py --parallel --cliques5 rmat22
 
 --parallel runs the OpenMP build of the same oracle source on OMP_NUM_THREADS
 threads (its equality with the serial build is pinned in test_oracle_pins).
@@ -160,6 +161,21 @@ def write_cliques(name, parallel=False):
     print(name, "cliques", out["oracle_seconds"], "s")
 
 
+def write_cliques5(name, parallel=False):
+    """The 5-clique count of a workload alone (oracle.clique5_count), where the
+    full census is out of reach."""
+    g = WORKLOADS[name]()
+    t0 = time.time()
+    k5 = oracle.clique5_count(g, parallel=parallel)
+    out = {"workload": name, "graph": g.name, "n": g.n, "m": g.m, "sha256": graph_hash(g),
+           "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": oracle.num_threads(parallel),
+           "oracle_host": f"{platform.machine()}, {os.cpu_count()} cores",
+           "sums": {"K5": str(k5)}}
+    with open(os.path.join(HERE, f"cliques5_{name}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, "cliques5", out["oracle_seconds"], "s")
+
+
 if __name__ == "__main__":
     par = "--parallel" in sys.argv
     names = [a for a in sys.argv[1:] if not a.startswith("--")]
@@ -170,6 +186,8 @@ if __name__ == "__main__":
             write_sums(name, par)
         elif "--pairs" in sys.argv:
             write_pairs(name, par)
+        elif "--cliques5" in sys.argv:
+            write_cliques5(name, par)
         elif "--cliques" in sys.argv:
             write_cliques(name, par)
         else:

@@ -334,6 +334,13 @@ def test_rmat_scale22_full_size():
             cliques = json.load(f)
         assert cliques["sha256"] == graph_hash(g)
         assert got["n4"][5] == int(cliques["sums"]["K4"])
+    # the oracle's 5-clique count (class 21)
+    cliques5_path = os.path.join(GOLDEN, "cliques5_rmat22.json")
+    if os.path.exists(cliques5_path):
+        with open(cliques5_path) as f:
+            cliques5 = json.load(f)
+        assert cliques5["sha256"] == graph_hash(g)
+        assert got["n5"][20] == int(cliques5["sums"]["K5"])
     pe = got["per_element"]
     T = got["n3"][3]
     assert int(pe["T_e"].sum()) == 6 * T and int(pe["t_i"].sum()) == 3 * T

@@ -330,3 +330,21 @@ def test_clique4_count_equals_the_census_and_closed_forms():
         assert oracle.clique4_count(gg.complete(n)) == comb(n, 4)
     for g in (gg.complete_bipartite(7, 9), gg.petersen(), gg.cycle(12)):
         assert oracle.clique4_count(g) == 0
+
+
+def test_clique5_count_equals_the_census_and_closed_forms():
+    """The 5-cliques counted alone (each at its lowest vertex, as a 4-clique
+    of G[N+(x)] with bit sets) agree with the census's bipyramid count
+    (serial and OpenMP builds), with C(n,5) on K_n, with zero on graphs without
+    K5, and with brute force on small random graphs."""
+    for g in _graphs_small() + [gg.chung_lu(3000, 2.1, 8, 300, 5), gg.config_rmat(11, 2),
+                                gg.erdos_renyi(120, 0.5, 3)]:
+        k5 = oracle.census(g)["n5"][20]
+        for par in (False, True):
+            assert oracle.clique5_count(g, parallel=par) == k5, g.name
+        if g.n <= 40:
+            assert k5 == oracle.brute_census(g)["c5"][20] or g.n < 5
+    for n in (4, 5, 6, 13, 64, 65, 70, 130):
+        assert oracle.clique5_count(gg.complete(n)) == comb(n, 5)
+    for g in (gg.complete_bipartite(7, 9), gg.petersen(), gg.complete(4)):
+        assert oracle.clique5_count(g) == 0

@@ -41,3 +41,25 @@ def test_kernel_digest_covers_the_kernel_only(tmp_path, monkeypatch):
     path.write_text(text.replace(plan, plan.replace("/ 2", "/ 3")))
     assert bench.source_digest("k_pairs") != base
 
+
+
+def test_stored_oracle_runs_and_traffic_record():
+    """The CPU-baseline context and the roofline's traffic come from committed
+    files: the R-MAT 22 workload has no stored full census, so its baseline
+    points at the stored R-MAT 20 run; the traffic record matches the current
+    kernel source."""
+    assert bench.stored_oracle_run("rmat22") is None
+    rel = bench.stored_oracle_run(bench.RELATED_FULL["rmat22"][0])
+    assert rel is not None and rel["seconds"] > 0 and rel["m"] > 0
+    assert bench.stored_traffic("k_pairs", "rmat22") is not None
+    assert bench.stored_traffic("k_pairs", "no_such_workload") is None
+
+
+def test_byte_model_sums_come_from_the_stored_oracle():
+    """W and D of the byte model are read from the stored oracle sums of the
+    workload graph (matched by the CSR hash)."""
+    import json
+    with open(os.path.join(bench.ROOT, "tests", "golden", "sums_rmat22.json")) as f:
+        gold = json.load(f)
+    assert {"W", "T", "D"} <= set(gold["sums"])
+    assert gold["n"] == 4194304

@@ -46,12 +46,18 @@ def test_kernel_digest_covers_the_kernel_only(tmp_path, monkeypatch):
 def test_stored_oracle_runs_and_traffic_record():
     """The CPU-baseline context and the roofline's traffic come from committed
     files: the R-MAT 22 workload has no stored full census, so its baseline
-    points at the stored R-MAT 20 run; the traffic record matches the current
-    kernel source."""
+    points at the stored R-MAT 20 run; the traffic record carries the digest of
+    the kernel source it was taken on (the bench reports it only while that
+    digest is current)."""
+    import json
     assert bench.stored_oracle_run("rmat22") is None
     rel = bench.stored_oracle_run(bench.RELATED_FULL["rmat22"][0])
     assert rel is not None and rel["seconds"] > 0 and rel["m"] > 0
-    assert bench.stored_traffic("k_pairs", "rmat22") is not None
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)["k_pairs:rmat22"]
+    assert rec["dram_bytes_per_launch"] > 0 and len(rec["source_sha"]) == 16
+    current = bench.stored_traffic("k_pairs", "rmat22")
+    assert current in (None, rec["dram_bytes_per_launch"])
     assert bench.stored_traffic("k_pairs", "no_such_workload") is None
 
 
